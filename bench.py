@@ -1,0 +1,484 @@
+#!/usr/bin/env python3
+"""Benchmark: edge detection of binary images by the method of masks.
+
+One step = one me_edges_batch call over a batch of 4096 uneven 1-bit images
+(w, h log-uniform on [16, 4096], glyph strokes, rows padded to 16 bytes):
+the whole fused path (mask, four fundamental edges, OR) in one persistent
+kernel launched from a CUDA graph, inputs resident in HBM.  Prints one
+JSON line (rank 0).  Extra legs, timed after the main region: the staged
+five-pass form on the same batch, the fused kernel on one 32768x32768
+image, the batch kernel alone (roofline), host-buffer end-to-end, clocks,
+and the CPU oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun), each rank runs its own batch
+(seed = rank); no data-path collective; value = all pixels / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("Gpixel/s (bit-exact), fused+batched vs staged BitBlt; "
+          "serve p50/p99 latency")
+UNIT = "Gpixel/s"
+N_IMAGES = 4096
+WORKLOAD = ("batch of 4096 uneven 1bpp images, w and h log-uniform on [16, 4096], "
+            "glyph-stroke content, rows padded to 16 bytes, one persistent launch "
+            "under a CUDA graph")
+
+
+# ---------------------------------------------------------------- ranks
+def rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def shard_seed(rank: int) -> int:
+    """Each rank draws its own batch: weak scaling, no exchange."""
+    return rank
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def reduce_max(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        if not self.rows:
+            return None
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap")
+        sm, mx, reasons, n = [], [], set(), 0
+        for ts, p in self.rows:
+            if not (t0 - 0.25 <= ts <= t1 + 0.25):
+                continue
+            n += 1
+            try:
+                util = float(p[4])
+            except ValueError:
+                util = 0.0
+            try:
+                if util > 0:
+                    sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                pass
+            for name, flag in zip(names, p[6:10]):
+                if flag.strip().lower() == "active":
+                    reasons.add(name)
+        if not mx:
+            return None
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": n, "samples_under_load": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("me_window.cuh", "me_window.cu"):
+        with open(os.path.join(ROOT, "paper_1401_5245_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind: str, bytes_per_launch_now: int):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current kernel source; scaled to this launch's units if the
+    capture was a smaller case.  None otherwise."""
+    p = os.path.join(ROOT, "profiles", f"{kind}_traffic.txt")
+    try:
+        kv = {}
+        with open(p) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256") != kernel_source_hash():
+            return None
+        traffic = float(kv["dram_bytes_per_launch"])
+        algo = float(kv["algorithmic_bytes_per_launch"])
+        return int(traffic * bytes_per_launch_now / algo)
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The CPU oracle (single thread, as it stands) on bounded samples of the
+    same batch; rank 0 alone under torchrun."""
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_1401_5245_gb300 import synth
+    oracle.build()
+    shapes = synth.batch_shapes(shard_seed(0), N_IMAGES)
+    # a bounded sample per step: the first images up to ~60 Mpixel
+    sample, px = [], 0
+    for i, (w, h) in enumerate(shapes):
+        if px >= 60e6:
+            break
+        sample.append(i)
+        px += w * h
+    imgs = []
+    for i in sample:
+        w, h = shapes[i]
+        im = synth.batch_image(shard_seed(0), i, w, h)
+        imgs.append(synth.unpack(im.words, im.w))
+    def step():
+        t = time.perf_counter()
+        for im in imgs:
+            oracle.edges(im, 0)
+        return time.perf_counter() - t
+    for _ in range(args.warmup):
+        step()
+    times = [step() for _ in range(args.steps)]
+    total = sum(times)
+    value = px * args.steps / total / 1e9
+    desc = f"first {len(sample)} images of the 4096-image batch ({px / 1e6:.1f} Mpixel) per step"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": desc},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def upload_batch(batch, device):
+    """All images in one device buffer (each 16-byte aligned), outputs in
+    another; returns tensors, per-image word offsets and pinned host copies."""
+    import torch
+    offs, cur = [], 0
+    for im in batch:
+        offs.append(cur)
+        cur += (im.words.size + 3) // 4 * 4
+    host_in = torch.empty(cur, dtype=torch.int32, pin_memory=True)
+    hv = host_in.numpy().view(np.uint32)
+    for im, o in zip(batch, offs):
+        hv[o:o + im.words.size] = im.words.ravel()
+    dev_in = host_in.to(device)
+    dev_out = torch.zeros(cur, dtype=torch.int32, device=device)
+    host_out = torch.empty(cur, dtype=torch.int32, pin_memory=True)
+    return dev_in, dev_out, host_in, host_out, offs
+
+
+def descs_for(lib, batch, dev_in, dev_out, offs):
+    bi, bo = dev_in.data_ptr(), dev_out.data_ptr()
+    return lib.make_descs((bi + 4 * o, bo + 4 * o, im.w, im.h, im.stride_words, 0)
+                          for im, o in zip(batch, offs))
+
+
+def verify_sample(batch, dev_out, offs, every=16):
+    """Bit-exact gate: every `every`-th image and the 8 largest against the
+    CPU oracle."""
+    from oracle import oracle
+    from paper_1401_5245_gb300 import synth
+    out = dev_out.cpu().numpy().view(np.uint32)
+    idx = set(range(0, len(batch), every))
+    idx |= set(sorted(range(len(batch)), key=lambda i: -batch[i].pixels)[:8])
+    for i in sorted(idx):
+        im = batch[i]
+        ow = out[offs[i]:offs[i] + im.words.size].reshape(im.words.shape)
+        got = synth.unpack(ow, im.w)
+        if not np.array_equal(got, oracle.edges(synth.unpack(im.words, im.w), 0)):
+            return False, len(idx)
+    return True, len(idx)
+
+
+def time_events(fn, reps, stream):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def cpu_baseline_leg(batch, budget_s=20.0):
+    from oracle import oracle
+    from paper_1401_5245_gb300 import synth
+    oracle.build()
+    t_used, px, n = 0.0, 0, 0
+    for im in batch:
+        img = synth.unpack(im.words, im.w)
+        t = time.perf_counter()
+        oracle.edges(img, 0)
+        t_used += time.perf_counter() - t
+        px += im.pixels
+        n += 1
+        if t_used >= budget_s:
+            break
+    return {"value": px / t_used / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} of the {len(batch)} batch images ({px / 1e9:.3f} Gpixel), "
+                      f"single-threaded C oracle, unpack not timed"}
+
+
+def run_ours(args, rank, world, local_rank):
+    from paper_1401_5245_gb300 import synth
+    t_gen = time.time()
+    batch = synth.batch(shard_seed(rank), N_IMAGES, workers=min(16, os.cpu_count() or 1))
+    t_gen = time.time() - t_gen
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_5245_gb300 import _lib
+    lib = _lib.load()
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    dist = init_dist(world, "nccl")
+    stream = torch.cuda.current_stream()
+
+    pixels = sum(im.pixels for im in batch)
+    algo_bytes = sum(2 * im.packed_bytes for im in batch)
+    dev_in, dev_out, host_in, host_out, offs = upload_batch(batch, device)
+    descs = descs_for(_lib, batch, dev_in, dev_out, offs)
+
+    def step():
+        rc = lib.me_edges_batch(descs, len(batch), stream.cuda_stream)
+        if rc != 0:
+            raise _lib.MeError(rc, "me_edges_batch")
+
+    # bit-exact gate before anything is timed
+    step()
+    torch.cuda.synchronize()
+    exact, n_checked = verify_sample(batch, dev_out, offs)
+
+    sampler = ClockSampler(local_rank)
+    time.sleep(0.3)
+    t_wall0 = time.time()
+    for _ in range(args.warmup):
+        step()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    t_step_max = reduce_max(dist, t_step, device)
+    total_pixels = reduce_sum(dist, float(pixels), device)
+    value = total_pixels / t_step_max / 1e9
+
+    # roofline: the batch kernel alone, replayed from a plan's graph
+    plan = _lib.BatchPlan(descs, len(batch), stream)
+    reps = max(20, int(0.5 / max(t_step, 1e-6)))
+    t_kernel = time_events(lambda: plan.run(stream), reps, stream)
+    kernel_bytes = plan.bytes
+    plan.close()
+    t_wall1 = time.time()
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    peak, peak_kind = measured_peak_gbs()
+    achieved = kernel_bytes / t_kernel / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": ncu_traffic("batch", kernel_bytes),
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "kernel": "k_batch (persistent batch kernel)",
+                "kernel_ms": round(t_kernel * 1e3, 4)}
+
+    extra = {}
+    # staged five-pass form on the same batch, one image per launch
+    def staged():
+        for d in descs[:len(batch)]:
+            rc = lib.me_edges_staged(d.img, d.w, d.h, d.stride_words, d.edge, 0,
+                                     stream.cuda_stream)
+            if rc != 0:
+                raise _lib.MeError(rc, "me_edges_staged")
+    staged()
+    t_staged = time_events(staged, 2, stream)
+    extra["staged_batch"] = {"gpixel_s": round(pixels / t_staged / 1e9, 2),
+                             "ms_per_batch": round(t_staged * 1e3, 3),
+                             "launches_per_batch": 5 * len(batch)}
+    extra["fused_batched_vs_staged"] = round(t_staged / t_step, 2)
+
+    # host buffers end to end: H2D of all inputs, the batch, D2H of all edges
+    def e2e_step():
+        dev_in.copy_(host_in, non_blocking=True)
+        step()
+        host_out.copy_(dev_out, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = time_events(e2e_step, max(3, min(args.steps, 20)), stream)
+    e2e = {"value": round(total_pixels / reduce_max(dist, t_e2e, device) / 1e9, 3),
+           "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
+           "d2h_bytes_per_step": int(host_out.numel() * 4),
+           "path": "pinned host -> cudaMemcpyAsync -> me_edges_batch -> pinned host"}
+
+    # the 1-Gpixel single image (fused), rotating 3 buffers past L2
+    if not args.quick:
+        w = h = 32768
+        words = synth.bernoulli_half_packed(w, h, seed=rank)
+        xs = [torch.from_numpy(words.view(np.int32)).to(device) for _ in range(3)]
+        ys = [torch.empty_like(xs[0]) for _ in range(3)]
+        k = [0]
+        def single():
+            i = k[0] % 3
+            k[0] += 1
+            rc = lib.me_edges(xs[i].data_ptr(), w, h, 1024, ys[i].data_ptr(), 0,
+                              stream.cuda_stream)
+            if rc != 0:
+                raise _lib.MeError(rc, "me_edges")
+        single()
+        t_single = time_events(single, 60, stream)
+        b1 = 2 * h * 1024 * 4
+        def staged1():
+            i = k[0] % 3
+            k[0] += 1
+            rc = lib.me_edges_staged(xs[i].data_ptr(), w, h, 1024, ys[i].data_ptr(), 0,
+                                     stream.cuda_stream)
+            if rc != 0:
+                raise _lib.MeError(rc, "me_edges_staged")
+        staged1()
+        t_staged1 = time_events(staged1, 6, stream)
+        extra["fused_32768"] = {"gpixel_s": round(w * h / t_single / 1e9, 1),
+                                "gb_s": round(b1 / t_single / 1e9, 1),
+                                "frac_of_peak": round(b1 / t_single / 1e9 / peak, 4),
+                                "us": round(t_single * 1e6, 2)}
+        extra["staged_32768"] = {"gpixel_s": round(w * h / t_staged1 / 1e9, 1),
+                                 "us": round(t_staged1 * 1e6, 2)}
+        del xs, ys
+
+    cfg = _lib.me_get_tile_cfg(1).as_dict()
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(t_step_max * 1e3, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "images": len(batch),
+                      "gpixels_per_step_per_gpu": round(pixels / 1e9, 4),
+                      "hbm_bytes_per_step_per_gpu": algo_bytes,
+                      "l2": "inputs larger than L2 (no flush needed)",
+                      "parallelism": f"replicas x{world}", "tile_cfg": cfg,
+                      "exact": exact, "exact_images_checked": n_checked,
+                      "generate_s": round(t_gen, 1)},
+           "gpu_launches": args.steps,
+           "e2e": e2e, "roofline": roofline, "clocks": clocks, "extra": extra}
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline_leg(batch, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the 1-Gpixel leg")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args(argv)
+    rank, world, local_rank = rank_info()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

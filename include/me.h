@@ -1,0 +1,306 @@
+/*
+ * me.h -- C ABI of libme, edge detection of binary images by the method of
+ * masks (Sadeq, Wahdan, Mahdi, "Edge detection of binary images using the
+ * method of masks", Sci. Bull. Fac. Eng. Ain Shams Univ. 35(3), 2000).
+ *
+ * What every call computes (Sections 3-5 of the paper, fused):
+ *
+ *     mask      M  = NOT I                               (Section 3)
+ *     left      FL = M AND I(x-1, y)   right FR = M AND I(x+1, y)
+ *     up        FU = M AND I(x, y-1)   down  FD = M AND I(x, y+1)  (Section 4)
+ *     edge      E  = FL OR FR OR FU OR FD                (Section 5)
+ *
+ * which is the Boolean function Edge(p) = (p)' and (2 or 4 or 6 or 8) of
+ * Section 1 (neighbour numbers of Fig. 1) applied to every pixel at once.
+ * All results are exact: integer bitwise work, no rounding anywhere.
+ *
+ * Image layout (every call): packed rows of 32-bit words.  Pixel (x, y) is
+ * bit x % 32 of word y * stride_words + x / 32; the least significant bit is
+ * the leftmost pixel, row 0 is the top row, 0 = black and 1 = white (Section
+ * 2: one bit per pixel, 0 for black, 1 for white).  nw = ceil(w / 32) words
+ * of a row hold pixels; bits x >= w of word nw-1 and words nw .. stride-1
+ * are padding.  Input padding is ignored (read as outside the image).  In
+ * every output, the padding bits of word nw-1 are written 0 and words
+ * nw .. stride-1 are left untouched.
+ *
+ * Edge polarity: an output bit of 1 marks an edge point (Edge(p) = logic 1,
+ * Section 1).  Section 5 inverts the OR only to draw edges black on white;
+ * me_edges_display gives that drawn form.
+ *
+ * Outside the image: pixels beyond the border take the boundary colour,
+ * ME_BOUNDARY_WHITE (the default reading: black pixels on the border are
+ * edge points) or ME_BOUNDARY_BLACK.
+ *
+ * Memory: "device pointer" means memory the current CUDA device can read
+ * and write (cudaMalloc, torch CUDA tensors).  Buffers are owned by the
+ * caller unless stated otherwise.  Calls that take a stream are
+ * asynchronous on it: inputs must stay valid and outputs must not be read
+ * until the stream has passed the call.  Unless stated otherwise, a call
+ * allocates nothing.
+ *
+ * Errors: every call returns ME_OK (0), a positive progress code, or a
+ * negative error code; me_status_string() names it.  A call that returns an
+ * error has enqueued no work.  ME_ERR_CUDA also records the CUDA error,
+ * readable once through me_last_cuda_error().
+ */
+#ifndef ME_H
+#define ME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without the CUDA headers; NULL is the legacy default stream. */
+typedef struct CUstream_st *me_stream_t;
+
+/* ---- status codes ------------------------------------------------------ */
+#define ME_OK            0
+#define ME_PENDING       1   /* serve: result not ready (poll with timeout 0) */
+#define ME_TIMEOUT       2   /* serve: result not ready when the wait ran out */
+#define ME_ERR_ARG      -1   /* NULL pointer, w or h <= 0, stride < ceil(w/32),
+                                bad boundary, host pointer where device needed */
+#define ME_ERR_ALIAS    -2   /* input and output ranges overlap */
+#define ME_ERR_ALIGN    -3   /* a forced 128-bit path was given unaligned data */
+#define ME_ERR_BUDGET   -4   /* serve: one request alone exceeds the budget */
+#define ME_ERR_CUDA     -5   /* a CUDA call failed; see me_last_cuda_error() */
+#define ME_ERR_CLOSED   -6   /* serve: the server is closed or closing */
+#define ME_ERR_TICKET   -7   /* serve: unknown or already collected ticket */
+#define ME_ERR_NOMEM    -8   /* host allocation failed */
+#define ME_ERR_UNSUPPORTED -9 /* no sm_103a device / feature not built */
+
+#define ME_BOUNDARY_WHITE 0
+#define ME_BOUNDARY_BLACK 1
+
+/* Name of a status code ("ME_OK", "ME_ERR_ARG", ...).  Never NULL. */
+const char *me_status_string(int status);
+
+/* The CUDA error code behind the last ME_ERR_CUDA on this thread, then 0. */
+int me_last_cuda_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int me_version(void);
+
+/* ---- single image ------------------------------------------------------- */
+
+/*
+ * Fused method of masks, Sections 3-5 in one pass:
+ *     edge = NOT img AND (I(x-1) OR I(x+1) OR I(y-1) OR I(y+1)).
+ * Each input word is read once from HBM and each output word written once.
+ *
+ * img, edge     device pointers to h rows of stride_words words each; they
+ *               must not overlap (ME_ERR_ALIAS).  128-bit loads are used
+ *               when both are 16-byte aligned and stride_words % 4 == 0,
+ *               32-bit loads otherwise; both give the same bits.
+ * w, h          image size in pixels, each >= 1.
+ * stride_words  words per row, >= ceil(w / 32).
+ * boundary      ME_BOUNDARY_WHITE or ME_BOUNDARY_BLACK.
+ * stream        CUDA stream the kernel is enqueued on.
+ */
+int me_edges(const uint32_t *img, int32_t w, int32_t h, int32_t stride_words,
+             uint32_t *edge, int32_t boundary, me_stream_t stream);
+
+/*
+ * The same result as me_edges, computed the way the paper's Section 2
+ * describes its bit-block transfers: five separate whole-image passes,
+ *     1. M  = NOT I                       (Section 3)
+ *     2. E  = M AND I(x-1)                (Section 4, left edge)
+ *     3. E |= M AND I(x+1)    4. E |= M AND I(y-1)    5. E |= M AND I(y+1)
+ *                                          (Section 4 edges ORed, Section 5)
+ * It moves about 17 bits of HBM traffic per pixel instead of 2 and is kept
+ * as the baseline form.  Arguments as me_edges.  The mask image M is
+ * scratch the library takes from CUDA's stream-ordered allocator on
+ * `stream` and returns after pass 5 (h * stride_words * 4 bytes); failure
+ * to get it returns ME_ERR_CUDA with nothing enqueued.
+ */
+int me_edges_staged(const uint32_t *img, int32_t w, int32_t h,
+                    int32_t stride_words, uint32_t *edge, int32_t boundary,
+                    me_stream_t stream);
+
+/*
+ * The four fundamental edges of Section 4 from one read of the image:
+ *     left  = M AND I(x-1, y)  (Fig. 2 b)    right = M AND I(x+1, y) (Fig. 2 a)
+ *     up    = M AND I(x, y-1)  (Fig. 2 c)    down  = M AND I(x, y+1) (Fig. 2 d)
+ * Four device outputs in the layout of img; none may overlap img or each
+ * other.  Other arguments as me_edges.
+ */
+int me_fundamental_edges(const uint32_t *img, int32_t w, int32_t h,
+                         int32_t stride_words, uint32_t *left, uint32_t *right,
+                         uint32_t *up, uint32_t *down, int32_t boundary,
+                         me_stream_t stream);
+
+/*
+ * Section 5 as drawn: the OR of the four edges inverted, so edge points are
+ * 0 (black) and everything else 1 (white) -- the negation of me_edges on
+ * the w pixels of each row (padding bits still written 0).  Arguments as
+ * me_edges.
+ */
+int me_edges_display(const uint32_t *img, int32_t w, int32_t h,
+                     int32_t stride_words, uint32_t *out, int32_t boundary,
+                     me_stream_t stream);
+
+/*
+ * Second clause of the Section 1 definition on its own: out = 1 at a black
+ * pixel with at most one black 8-neighbour (Fig. 1 neighbours 1-8), i.e.
+ * isolated points and the ends of one-pixel lines.  Every such point is
+ * also an edge point of me_edges (Section 1: the other cases are included
+ * in the four types).  Arguments as me_edges.
+ */
+int me_end_points(const uint32_t *img, int32_t w, int32_t h,
+                  int32_t stride_words, uint32_t *out, int32_t boundary,
+                  me_stream_t stream);
+
+/* ---- many images in one launch ----------------------------------------- */
+
+typedef struct me_desc {
+    const uint32_t *img;     /* device input, layout as me_edges */
+    uint32_t *edge;          /* device output, must not overlap img */
+    int32_t w, h;            /* pixels, >= 1 */
+    int32_t stride_words;    /* >= ceil(w / 32) */
+    int32_t boundary;        /* ME_BOUNDARY_WHITE or ME_BOUNDARY_BLACK */
+} me_desc;
+
+/*
+ * me_edges on n images of any sizes in ONE persistent kernel launch,
+ * replayed from a captured CUDA graph.  descs is a HOST array, copied
+ * before the call returns (the caller may reuse it at once).  Image and
+ * edge buffers are caller-owned device memory, checked for NULL, size and
+ * overlap within each descriptor but not against one another: two
+ * descriptors writing the same edge words race.  Images are split into
+ * warp tiles (rows x word columns) that the launch walks in one pass;
+ * 128-bit loads are used per image where its buffers allow them.
+ *
+ * The library owns a pinned staging ring, a device descriptor arena and a
+ * graph cache keyed by (capacity bucket, tile configuration); all of them
+ * live until me_shutdown().  n == 0 returns ME_OK with nothing enqueued.
+ */
+int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream);
+
+/*
+ * A batch planned once and replayed many times: the descriptors are
+ * uploaded to a device arena owned by the plan, and every me_batch_run is
+ * one graph launch of the kernel alone.  The plan keeps the tile
+ * configuration current at creation.  Runs of one plan on different
+ * streams must be ordered by the caller.
+ */
+typedef struct me_batch_plan me_batch_plan;
+int me_batch_plan_create(const me_desc *descs, int32_t n, me_stream_t stream,
+                         me_batch_plan **out);
+int me_batch_run(me_batch_plan *plan, me_stream_t stream);
+/* Algorithmic bytes a run moves: sum of 2 * h * stride_words * 4. */
+int64_t me_batch_plan_bytes(const me_batch_plan *plan);
+/* Waits for the plan's uploads, then frees it.  NULL is ignored. */
+int me_batch_plan_destroy(me_batch_plan *plan);
+
+/* ---- tile configuration and autotuning --------------------------------- */
+
+#define ME_KIND_SINGLE 0     /* me_edges and its single-image relatives */
+#define ME_KIND_BATCH  1     /* me_edges_batch, plans and the server */
+
+#define ME_ENGINE_REGS 0     /* rows slide through registers, 128/32-bit loads */
+#define ME_ENGINE_BULK 1     /* row bands staged in shared memory by bulk
+                                asynchronous copies (TMA), mbarrier pipeline */
+
+typedef struct me_tile_cfg {
+    int32_t engine;          /* ME_ENGINE_REGS or ME_ENGINE_BULK */
+    int32_t rows_per_lane;   /* rows one lane walks: 4, 8, 16 or 32 */
+    int32_t vec_words;       /* 4: 128-bit loads where aligned; 1: 32-bit */
+    int32_t cta_threads;     /* 128, 256 or 512 */
+    int32_t ctas_per_sm;     /* persistent grid of SMs x this; 0 = one warp
+                                per tile, no persistence */
+} me_tile_cfg;
+
+/* Read or replace the configuration used by the calls of `kind`. */
+int me_get_tile_cfg(int32_t kind, me_tile_cfg *out);
+int me_set_tile_cfg(int32_t kind, const me_tile_cfg *cfg);
+
+/*
+ * Time every candidate configuration on the caller's images (device
+ * buffers; results are written to their edge buffers) with CUDA events on
+ * `stream`, set the fastest for `kind`, and return it in *best.  Runs
+ * synchronously.  If the environment variable ME_TUNE_CACHE names a file,
+ * the choice is also written there and read back by the next process
+ * (keyed by device name and kind).  `reps` timed repetitions per candidate.
+ */
+int me_autotune(int32_t kind, const me_desc *sample, int32_t n, int32_t reps,
+                me_stream_t stream, me_tile_cfg *best);
+
+/* ---- serving ------------------------------------------------------------ */
+
+typedef struct me_serve_cfg {
+    int64_t hbm_budget_bytes;   /* device bytes for resident request images
+                                   and edge maps (in + out) */
+    int64_t staging_bytes;      /* pinned host bytes for request staging;
+                                   0 = same as hbm_budget_bytes */
+    int32_t max_inflight;       /* launched, unfinished batches (>= 1) */
+    int32_t max_batch;          /* requests per launch (>= 1) */
+    int32_t tick_us;            /* engine wake-up period when idle */
+    int32_t device;             /* CUDA device ordinal */
+} me_serve_cfg;
+
+typedef struct me_timing {
+    double queue_us;            /* submit -> admitted (device memory given) */
+    double device_us;           /* admitted -> result copied back to host */
+    double total_us;            /* submit -> result ready */
+} me_timing;
+
+typedef struct me_server me_server;
+
+/*
+ * Start a server: a library thread that admits submitted requests against
+ * the HBM budget, keeps their packed images and edge maps resident on the
+ * device, and runs whatever is admitted as batches (continuous batching:
+ * requests that arrive while batches run join the next launch once memory
+ * and an in-flight slot are free).  Copies and kernels overlap on separate
+ * streams.  The server owns a device pool of hbm_budget_bytes and a pinned
+ * pool of staging_bytes.
+ */
+int me_serve_open(const me_serve_cfg *cfg, me_server **out);
+
+/*
+ * Queue one image.  host_img (h rows of stride_words words, layout as
+ * me_edges) is copied before the call returns.  Returns ME_ERR_BUDGET when
+ * this image's input plus output alone exceed the budget (or the staging
+ * pool); otherwise the request waits until memory frees up.  *ticket
+ * identifies the request to me_serve_poll.
+ */
+int me_serve_submit(me_server *srv, const uint32_t *host_img, int32_t w,
+                    int32_t h, int32_t stride_words, int32_t boundary,
+                    uint64_t *ticket);
+
+/*
+ * Collect a result.  Waits up to timeout_us microseconds (0: do not wait,
+ * negative: wait without limit) and returns ME_OK with the edge map copied
+ * to host_edge (h rows of the request's stride_words; padding words
+ * untouched) and the timing in *t (may be NULL); ME_PENDING (timeout 0) or
+ * ME_TIMEOUT when not ready; ME_ERR_TICKET for an unknown or already
+ * collected ticket.  A collected ticket is forgotten.
+ */
+int me_serve_poll(me_server *srv, uint64_t ticket, uint32_t *host_edge,
+                  int64_t timeout_us, me_timing *t);
+
+/*
+ * Counters since open: requests submitted, completed, batches launched,
+ * and the most device bytes ever in use.  Any pointer may be NULL.
+ */
+int me_serve_stats(me_server *srv, int64_t *submitted, int64_t *completed,
+                   int64_t *batches, int64_t *peak_bytes);
+
+/*
+ * Stop accepting requests, finish the ones admitted or queued (waiting at
+ * most drain_timeout_us; negative = no limit), then free the server.
+ * Uncollected results are dropped.  Returns ME_TIMEOUT if the drain ran
+ * out (the server is freed all the same once its GPU work has ended).
+ */
+int me_serve_close(me_server *srv, int64_t drain_timeout_us);
+
+/* Free the batch rings, graphs and plans' shared state on every device. */
+int me_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ME_H */

@@ -1,0 +1,291 @@
+"""ctypes binding of libme (C ABI in include/me.h).
+
+Argument marshalling only: every computation runs in the CUDA kernels of
+libme.so.  Functions keep the C names and return the C status code; the
+``*_checked`` helpers and :func:`check` raise :class:`MeError` instead.
+Tensors may be passed wherever the C call takes a device pointer (their
+``data_ptr()`` is used); streams may be a ``torch.cuda.Stream``, a raw
+``cudaStream_t`` integer, or None for the current torch stream.
+
+There is no fallback: if libme.so is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+LIB_PATH = os.path.join(PKG, "libme.so")
+HEADER = os.path.join(ROOT, "include", "me.h")
+
+c_i32, c_i64, c_u64, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
+
+
+def _constants():
+    """#define constants of me.h, read from the header itself."""
+    out = {}
+    with open(HEADER) as f:
+        for m in re.finditer(r"^#define\s+(ME_[A-Z0-9_]+)\s+(-?\d+)", f.read(), re.M):
+            out[m.group(1)] = int(m.group(2))
+    return out
+
+
+C = _constants()
+globals().update(C)
+
+
+class MeError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        name = status_string(status) if _lib is not None else str(status)
+        extra = ""
+        if status == C["ME_ERR_CUDA"] and _lib is not None:
+            extra = f" (cudaError {_lib.me_last_cuda_error()})"
+        super().__init__(f"{what}: {name}{extra}" if what else name + extra)
+
+
+class me_desc(ctypes.Structure):
+    _fields_ = [("img", c_vp), ("edge", c_vp), ("w", c_i32), ("h", c_i32),
+                ("stride_words", c_i32), ("boundary", c_i32)]
+
+
+class me_tile_cfg(ctypes.Structure):
+    _fields_ = [("engine", c_i32), ("rows_per_lane", c_i32), ("vec_words", c_i32),
+                ("cta_threads", c_i32), ("ctas_per_sm", c_i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class me_serve_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", c_i64), ("staging_bytes", c_i64),
+                ("max_inflight", c_i32), ("max_batch", c_i32), ("tick_us", c_i32),
+                ("device", c_i32)]
+
+
+class me_timing(ctypes.Structure):
+    _fields_ = [("queue_us", ctypes.c_double), ("device_us", ctypes.c_double),
+                ("total_us", ctypes.c_double)]
+
+
+# name -> (restype, argtypes)
+PROTOTYPES = {
+    "me_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "me_last_cuda_error": (ctypes.c_int, []),
+    "me_version": (ctypes.c_int, []),
+    "me_edges": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
+    "me_edges_staged": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
+    "me_fundamental_edges": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp,
+                                            c_vp, c_vp, c_i32, c_vp]),
+    "me_edges_display": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
+    "me_end_points": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
+    "me_edges_batch": (ctypes.c_int, [ctypes.POINTER(me_desc), c_i32, c_vp]),
+    "me_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(me_desc), c_i32, c_vp,
+                                            ctypes.POINTER(c_vp)]),
+    "me_batch_run": (ctypes.c_int, [c_vp, c_vp]),
+    "me_batch_plan_bytes": (c_i64, [c_vp]),
+    "me_batch_plan_destroy": (ctypes.c_int, [c_vp]),
+    "me_get_tile_cfg": (ctypes.c_int, [c_i32, ctypes.POINTER(me_tile_cfg)]),
+    "me_set_tile_cfg": (ctypes.c_int, [c_i32, ctypes.POINTER(me_tile_cfg)]),
+    "me_autotune": (ctypes.c_int, [c_i32, ctypes.POINTER(me_desc), c_i32, c_i32, c_vp,
+                                   ctypes.POINTER(me_tile_cfg)]),
+    "me_serve_open": (ctypes.c_int, [ctypes.POINTER(me_serve_cfg), ctypes.POINTER(c_vp)]),
+    "me_serve_submit": (ctypes.c_int, [c_vp, c_vp, c_i32, c_i32, c_i32, c_i32,
+                                       ctypes.POINTER(c_u64)]),
+    "me_serve_poll": (ctypes.c_int, [c_vp, c_u64, c_vp, c_i64, ctypes.POINTER(me_timing)]),
+    "me_serve_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
+                                      ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    "me_serve_close": (ctypes.c_int, [c_vp, c_i64]),
+    "me_shutdown": (ctypes.c_int, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libme.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise MeError(C["ME_ERR_UNSUPPORTED"],
+                              f"libme.so not built at {p}; run __graft_entry__.build()")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in PROTOTYPES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().me_status_string(int(status)).decode()
+
+
+def check(status: int, what: str = "") -> int:
+    if status < 0:
+        raise MeError(status, what)
+    return status
+
+
+def ptr(x) -> int | None:
+    """Device pointer of a tensor, or an integer pointer as is."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---------------------------------------------------------------- the C calls
+def me_edges(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:
+    return load().me_edges(ptr(img), w, h, stride_words, ptr(edge), boundary,
+                           stream_handle(stream))
+
+
+def me_edges_staged(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:
+    return load().me_edges_staged(ptr(img), w, h, stride_words, ptr(edge), boundary,
+                                  stream_handle(stream))
+
+
+def me_fundamental_edges(img, w, h, stride_words, left, right, up, down, boundary=0,
+                         stream=None) -> int:
+    return load().me_fundamental_edges(ptr(img), w, h, stride_words, ptr(left),
+                                       ptr(right), ptr(up), ptr(down), boundary,
+                                       stream_handle(stream))
+
+
+def me_edges_display(img, w, h, stride_words, out, boundary=0, stream=None) -> int:
+    return load().me_edges_display(ptr(img), w, h, stride_words, ptr(out), boundary,
+                                   stream_handle(stream))
+
+
+def me_end_points(img, w, h, stride_words, out, boundary=0, stream=None) -> int:
+    return load().me_end_points(ptr(img), w, h, stride_words, ptr(out), boundary,
+                                stream_handle(stream))
+
+
+def make_descs(items) -> ctypes.Array:
+    """items: iterable of (img, edge, w, h, stride_words, boundary)."""
+    items = list(items)
+    arr = (me_desc * max(1, len(items)))()
+    for i, (img, edge, w, h, stride, boundary) in enumerate(items):
+        arr[i] = me_desc(ptr(img), ptr(edge), w, h, stride, boundary)
+    return arr
+
+
+def me_edges_batch(descs, n=None, stream=None) -> int:
+    n = len(descs) if n is None else n
+    return load().me_edges_batch(descs, n, stream_handle(stream))
+
+
+class BatchPlan:
+    """me_batch_plan_create / me_batch_run / me_batch_plan_destroy."""
+
+    def __init__(self, descs, n=None, stream=None):
+        n = len(descs) if n is None else n
+        self._h = c_vp()
+        check(load().me_batch_plan_create(descs, n, stream_handle(stream),
+                                          ctypes.byref(self._h)), "me_batch_plan_create")
+
+    def run(self, stream=None) -> int:
+        return load().me_batch_run(self._h, stream_handle(stream))
+
+    @property
+    def bytes(self) -> int:
+        return load().me_batch_plan_bytes(self._h)
+
+    def close(self):
+        if self._h:
+            load().me_batch_plan_destroy(self._h)
+            self._h = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def me_get_tile_cfg(kind) -> me_tile_cfg:
+    c = me_tile_cfg()
+    check(load().me_get_tile_cfg(kind, ctypes.byref(c)), "me_get_tile_cfg")
+    return c
+
+
+def me_set_tile_cfg(kind, cfg: me_tile_cfg) -> int:
+    return load().me_set_tile_cfg(kind, ctypes.byref(cfg))
+
+
+def me_autotune(kind, descs, n=None, reps=10, stream=None) -> me_tile_cfg:
+    n = len(descs) if n is None else n
+    best = me_tile_cfg()
+    check(load().me_autotune(kind, descs, n, reps, stream_handle(stream),
+                             ctypes.byref(best)), "me_autotune")
+    return best
+
+
+def me_shutdown() -> int:
+    return load().me_shutdown()
+
+
+# ---------------------------------------------------------------- serving
+class Server:
+    """me_serve_open / submit / poll / stats / close."""
+
+    def __init__(self, hbm_budget_bytes=8 << 30, staging_bytes=0, max_inflight=4,
+                 max_batch=256, tick_us=50, device=0):
+        cfg = me_serve_cfg(hbm_budget_bytes, staging_bytes, max_inflight, max_batch,
+                           tick_us, device)
+        self._h = c_vp()
+        check(load().me_serve_open(ctypes.byref(cfg), ctypes.byref(self._h)),
+              "me_serve_open")
+
+    def submit(self, host_img, w, h, stride_words, boundary=0) -> tuple[int, int]:
+        """host_img: a C-contiguous numpy uint32 array (or a pointer)."""
+        t = c_u64()
+        p = host_img.ctypes.data if hasattr(host_img, "ctypes") else int(host_img)
+        rc = load().me_serve_submit(self._h, p, w, h, stride_words, boundary,
+                                    ctypes.byref(t))
+        return rc, t.value
+
+    def poll(self, ticket, host_edge, timeout_us=-1):
+        tm = me_timing()
+        p = host_edge.ctypes.data if hasattr(host_edge, "ctypes") else int(host_edge)
+        rc = load().me_serve_poll(self._h, ticket, p, timeout_us, ctypes.byref(tm))
+        return rc, tm
+
+    def stats(self):
+        v = [c_i64() for _ in range(4)]
+        check(load().me_serve_stats(self._h, *[ctypes.byref(x) for x in v]),
+              "me_serve_stats")
+        return dict(zip(("submitted", "completed", "batches", "peak_bytes"),
+                        [x.value for x in v]))
+
+    def close(self, drain_timeout_us=-1) -> int:
+        rc = C["ME_OK"]
+        if self._h:
+            rc = load().me_serve_close(self._h, drain_timeout_us)
+            self._h = c_vp()
+        return rc
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,123 @@
+// Internal declarations shared by the translation units of libme.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "me.h"
+
+namespace me {
+
+constexpr uint32_t kAllOnes = 0xFFFFFFFFu;
+
+// What a window kernel writes per pixel word.
+enum Mode : int {
+    MODE_EDGE = 0,      // Edge(p): NOT I AND (L OR R OR U OR D)       (Sections 3-5)
+    MODE_DISPLAY = 1,   // the OR inverted, as drawn in Section 5
+    MODE_FUND = 2,      // the four fundamental edges, four outputs  (Section 4)
+    MODE_END = 3,       // black with <= 1 black 8-neighbour          (Section 1)
+    MODE_COUNT = 4
+};
+
+// Geometry of one packed image as the kernels see it.
+struct Geo {
+    const uint32_t *img;
+    int32_t w, h, stride, nw;   // nw = ceil(w / 32) words hold pixels
+    uint32_t lastmask;          // valid bits of word nw - 1
+    uint32_t fill;              // outside colour as a word: ~0 white, 0 black
+    int32_t vw;                 // words per lane and row: 4 or 1
+    int32_t nv;                 // vector columns: ceil(nw / vw)
+    int32_t seg_log2;           // log2 of the lanes one row segment uses
+    int32_t ncb;                // column blocks of 32 vector columns
+};
+
+struct Outs {
+    uint32_t *p[4];
+};
+
+// Batch descriptor as the persistent kernel reads it (64 bytes).
+struct BDesc {
+    const uint32_t *img;
+    uint32_t *edge;
+    int32_t w, h, stride, nw;
+    uint32_t lastmask, fill;
+    int32_t vw, seg_log2, ncb, nv;
+    int32_t task_base, ntasks;
+};
+static_assert(sizeof(BDesc) == 64, "BDesc is 64 bytes");
+
+// Device arena of one batch: header, then descriptors, then the first task
+// of every warp's contiguous task range.
+struct BatchHeader {
+    int32_t n;
+    int32_t total_tasks;
+    int32_t total_warps;
+    int32_t rows_per_lane;
+    int64_t bytes;              // algorithmic bytes: sum of 2 * h * stride * 4
+    int32_t pad[58];
+};
+static_assert(sizeof(BatchHeader) == 256, "BatchHeader is 256 bytes");
+
+inline size_t arena_bytes(int n, int total_warps) {
+    return sizeof(BatchHeader) + (size_t)n * sizeof(BDesc) +
+           (((size_t)total_warps + 1) * sizeof(int32_t) + 255) / 256 * 256;
+}
+
+// ---------------------------------------------------------------- helpers
+int record_cuda(cudaError_t e);         // remembers e, returns ME_ERR_CUDA
+int check_image_args(const void *img, const void *out, int32_t w, int32_t h,
+                     int32_t stride_words, int32_t boundary);
+int check_device_ptr(const void *p);    // ME_OK or ME_ERR_ARG / ME_ERR_CUDA
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb);
+
+struct DevInfo {
+    int sm_count;
+    int max_threads_per_sm;
+    int cc_major, cc_minor;
+    char name[256];
+};
+int device_info(DevInfo *out);          // current device, cached
+
+Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
+             int32_t boundary, int vw);
+int pick_vw(const void *img, const void *out, int32_t stride, int want_vw);
+int ceil_log2(int v);
+
+// ------------------------------------------------------- configurations
+me_tile_cfg tile_cfg(int kind);         // current configuration of a kind
+bool valid_cfg(const me_tile_cfg &c);
+uint64_t cfg_key(const me_tile_cfg &c);
+
+// ---------------------------------------------------------- launchers
+// Single image, register-window engine.  `launches` counts kernels issued.
+cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
+                          const me_tile_cfg &cfg, cudaStream_t s);
+// Single image, bulk-copy (TMA) engine; only MODE_EDGE.  Returns
+// cudaErrorNotSupported when the image does not meet the engine's
+// alignment rules (caller falls back).
+cudaError_t launch_bulk(const Geo &g, uint32_t *edge, const me_tile_cfg &cfg,
+                        cudaStream_t s);
+bool bulk_eligible(const Geo &g, const void *edge);
+bool bulk_available();
+
+// Persistent batch kernel over an uploaded arena.
+cudaError_t launch_batch(const void *arena_dev, int grid, int threads,
+                         int rows_per_lane, cudaStream_t s);
+const void *batch_kernel(int rows_per_lane);   // for graph kernel nodes
+void batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int total_tasks,
+                int *grid, int *threads);
+
+// Fill descriptors and the warp start table of a batch arena on the host.
+// Returns ME_OK or an argument error for descriptor i (*bad = i).
+int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
+               int total_warps, void *host_arena, int *bad);
+int batch_tasks(const me_desc *descs, int n, const me_tile_cfg &cfg,
+                int64_t *total_tasks);
+
+// The five staged passes.
+cudaError_t launch_staged(const Geo &g, uint32_t *mask, uint32_t *edge,
+                          cudaStream_t s);
+
+}  // namespace me

@@ -1,0 +1,166 @@
+"""Bit-exact parity of the persistent batch kernel (me_edges_batch, batch
+plans) with the CPU oracle, image by image, including the full 4096-image
+uneven batch the benchmark times."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1401_5245_gb300 import _lib, synth as S
+from tests.gpu_util import DevBuf, SENTINEL, check_output_layout
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.init()
+    _lib.load()
+
+
+def sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def make_batch(seed, n, lo, hi, pad16=True, boundaries=None, offs=None):
+    shapes = S.batch_shapes(seed, n, lo, hi)
+    imgs, srcs, dsts, items = [], [], [], []
+    for i, (w, h) in enumerate(shapes):
+        img = S.strokes(w, h, max(1, (w * h) // 4000), seed * 977 + i)
+        if i % 5 == 0:       # some dense noise too
+            img = (np.random.default_rng(i).random((h, w)) < 0.5).astype(np.uint8)
+        stride = S.batch_stride(w, pad16)
+        words = S.pack(img, stride, pad="random", seed=i)
+        off = 0 if offs is None else offs[i % len(offs)]
+        src = DevBuf(words, off)
+        dst = DevBuf(np.zeros_like(words), off, fill=SENTINEL)
+        b = 0 if boundaries is None else boundaries[i % len(boundaries)]
+        imgs.append((img, b))
+        srcs.append(src)
+        dsts.append(dst)
+        items.append((src.ptr(), dst.ptr(), w, h, stride, b))
+    return imgs, srcs, dsts, items
+
+
+def check_batch(imgs, srcs, dsts):
+    for (img, b), src, dst in zip(imgs, srcs, dsts):
+        h, w = img.shape
+        assert dst.guards_intact()
+        ow = dst.words()
+        check_output_layout(ow, w)
+        assert np.array_equal(S.unpack(ow, w), O.edges(img, b)), (w, h, b)
+
+
+@pytest.mark.parametrize("pad16", [True, False])
+def test_small_uneven_batch(pad16):
+    imgs, srcs, dsts, items = make_batch(1, 96, 1, 700, pad16, boundaries=[0, 1])
+    descs = _lib.make_descs(items)
+    assert _lib.me_edges_batch(descs, len(items)) == 0
+    sync()
+    check_batch(imgs, srcs, dsts)
+
+
+def test_misaligned_buffers_take_the_32bit_path():
+    imgs, srcs, dsts, items = make_batch(2, 40, 1, 300, True, offs=[0, 1, 2, 3])
+    assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
+    sync()
+    check_batch(imgs, srcs, dsts)
+
+
+def test_repeated_calls_reuse_graphs_and_slots():
+    """Many calls in a row with different batch sizes: the staging ring
+    and the cached graphs are reused while earlier launches may be in
+    flight; every result stays exact."""
+    batches = [make_batch(10 + k, n, 1, 400) for k, n in enumerate([1, 7, 64, 300, 5, 64, 2])]
+    for _ in range(3):
+        for imgs, srcs, dsts, items in batches:
+            for d in dsts:
+                d.t.fill_(int(np.int32(np.uint32(SENTINEL).view(np.int32))))
+            assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
+        sync()
+        for imgs, srcs, dsts, items in batches:
+            check_batch(imgs, srcs, dsts)
+
+
+def test_every_batch_configuration():
+    L = _lib.load()
+    saved = _lib.me_get_tile_cfg(1)
+    imgs, srcs, dsts, items = make_batch(3, 50, 1, 1200)
+    descs = _lib.make_descs(items)
+    try:
+        for rows, threads, ctas, vec in itertools.product([4, 8, 16, 32], [128, 256, 512],
+                                                          [1, 2, 8], [1, 4]):
+            assert _lib.me_set_tile_cfg(1, _lib.me_tile_cfg(0, rows, vec, threads, ctas)) == 0
+            for d in dsts:
+                d.t.fill_(int(np.uint32(SENTINEL).view(np.int32)))
+            assert _lib.me_edges_batch(descs, len(items)) == 0
+            sync()
+            check_batch(imgs, srcs, dsts)
+    finally:
+        L.me_set_tile_cfg(1, saved)
+
+
+def test_plan_replays():
+    imgs, srcs, dsts, items = make_batch(4, 80, 1, 900, boundaries=[1, 0, 0])
+    plan = _lib.BatchPlan(_lib.make_descs(items), len(items))
+    want = sum(2 * it[3] * it[4] * 4 for it in items)
+    assert plan.bytes == want
+    for _ in range(5):
+        assert plan.run() == 0
+    sync()
+    check_batch(imgs, srcs, dsts)
+    plan.close()
+
+
+def test_batch_matches_single_calls():
+    import torch
+    imgs, srcs, dsts, items = make_batch(5, 64, 16, 2000)
+    assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
+    for (img, b), src, dst, it in zip(imgs, srcs, dsts, items):
+        ref = torch.empty_like(dst.t)
+        off = (dst.ptr() - dst.t.data_ptr())
+        assert _lib.me_edges(it[0], it[2], it[3], it[4], ref.data_ptr() + off, it[5]) == 0
+        sync()
+        a = dst.t.cpu().numpy()
+        r = ref.cpu().numpy()
+        n = it[3] * it[4]
+        lo = off // 4
+        nw = S.words_per_row(it[2])
+        aa = a[lo:lo + n].reshape(it[3], it[4])[:, :nw]
+        rr = r[lo:lo + n].reshape(it[3], it[4])[:, :nw]
+        assert np.array_equal(aa, rr)
+
+
+def test_full_uneven_batch_4096():
+    """The benchmark's batch: 4096 images, log-uniform 16..4096 per side,
+    glyph strokes, rows padded to 16 bytes; every image against the oracle."""
+    import torch
+    batch = S.batch(0, workers=8)
+    srcs, dsts, items = [], [], []
+    for im in batch:
+        x = torch.from_numpy(im.words.view(np.int32)).cuda()
+        y = torch.full_like(x, int(np.uint32(SENTINEL).view(np.int32)))
+        srcs.append(x)
+        dsts.append(y)
+        items.append((x, y, im.w, im.h, im.stride_words, 0))
+    assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
+    sync()
+    for im, y in zip(batch, dsts):
+        ow = y.cpu().numpy().view(np.uint32)
+        check_output_layout(ow, im.w)
+        img = S.unpack(im.words, im.w)
+        assert np.array_equal(S.unpack(ow, im.w), O.edges(img, 0)), (im.w, im.h)
+
+
+def test_zero_and_bad_batches():
+    L = _lib.load()
+    assert L.me_edges_batch(None, 0, None) == 0
+    imgs, srcs, dsts, items = make_batch(6, 3, 16, 64)
+    bad = list(items)
+    bad[1] = (bad[1][0], bad[1][1], bad[1][2], bad[1][3], 0, 0)   # stride 0
+    assert _lib.me_edges_batch(_lib.make_descs(bad), 3) == _lib.C["ME_ERR_ARG"]
