@@ -70,6 +70,7 @@ typedef struct CUstream_st *me_stream_t;
 #define ME_ERR_TICKET   -7   /* serve: unknown or already collected ticket */
 #define ME_ERR_NOMEM    -8   /* host allocation failed */
 #define ME_ERR_UNSUPPORTED -9 /* no sm_103a device / feature not built */
+#define ME_ERR_TOO_BIG  -10  /* image larger than me_edges_staged_static holds */
 
 #define ME_BOUNDARY_WHITE 0
 #define ME_BOUNDARY_BLACK 1
@@ -118,6 +119,28 @@ int me_edges(const uint32_t *img, int32_t w, int32_t h, int32_t stride_words,
 int me_edges_staged(const uint32_t *img, int32_t w, int32_t h,
                     int32_t stride_words, uint32_t *edge, int32_t boundary,
                     me_stream_t stream);
+
+/*
+ * me_edges_staged without any allocation, for callers that cannot allocate
+ * device memory while they run: code under a framework's caching allocator
+ * that owns the whole device, real-time loops where an allocation may block
+ * or fail, and processes whose device memory is capped after start-up.
+ * (The paper has no counterpart; it is a deployment variant of the staged
+ * form.)  The mask image lives in one fixed device array built into the
+ * library, ME_STATIC_MASK_WORDS words (4 MiB), which every GPU that loads
+ * the library keeps until the process exits.  Images with
+ * h * stride_words > ME_STATIC_MASK_WORDS return ME_ERR_TOO_BIG with nothing
+ * enqueued.  The first call on a device looks up the array's device address
+ * (no allocation); make that first call before any stream capture.  All
+ * calls on a device share the array, so calls whose GPU work may overlap
+ * (unordered streams) race and must be serialised by the caller.  Nothing
+ * is read from the array before the call has written it.  Other arguments
+ * and results as me_edges_staged.
+ */
+#define ME_STATIC_MASK_WORDS 1048576
+int me_edges_staged_static(const uint32_t *img, int32_t w, int32_t h,
+                           int32_t stride_words, uint32_t *edge, int32_t boundary,
+                           me_stream_t stream);
 
 /*
  * The four fundamental edges of Section 4 from one read of the image:

@@ -78,6 +78,8 @@ PROTOTYPES = {
     "me_version": (ctypes.c_int, []),
     "me_edges": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
     "me_edges_staged": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
+    "me_edges_staged_static": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32,
+                                              c_vp]),
     "me_fundamental_edges": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp,
                                             c_vp, c_vp, c_i32, c_vp]),
     "me_edges_display": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
@@ -161,6 +163,11 @@ def me_edges(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:
 def me_edges_staged(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:
     return load().me_edges_staged(ptr(img), w, h, stride_words, ptr(edge), boundary,
                                   stream_handle(stream))
+
+
+def me_edges_staged_static(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:
+    return load().me_edges_staged_static(ptr(img), w, h, stride_words, ptr(edge), boundary,
+                                         stream_handle(stream))
 
 
 def me_fundamental_edges(img, w, h, stride_words, left, right, up, down, boundary=0,

@@ -149,6 +149,7 @@ const char *me_status_string(int s) {
         case ME_ERR_TICKET: return "ME_ERR_TICKET";
         case ME_ERR_NOMEM: return "ME_ERR_NOMEM";
         case ME_ERR_UNSUPPORTED: return "ME_ERR_UNSUPPORTED";
+        case ME_ERR_TOO_BIG: return "ME_ERR_TOO_BIG";
         default: return "ME_UNKNOWN_STATUS";
     }
 }
