@@ -465,8 +465,50 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_profile_case(case: str, launches: int, cfg: str | None = None):
+    """A few launches of one kernel on a case small enough for an ncu
+    capture (inputs still larger than L2): 'batch' = the 4096-image batch
+    kernel; 'single' = me_edges on one 32768 x 32768 image (256 MiB).
+    cfg: optional tile configuration 'engine,rows,vec,threads,ctas,kb,stages'."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1401_5245_gb300 import _lib, synth
+    lib = _lib.load()
+    if cfg:
+        kind = 1 if case == "batch" else 0
+        _lib.check(_lib.me_set_tile_cfg(kind, _lib.me_tile_cfg(*map(int, cfg.split(",")))),
+                   "me_set_tile_cfg")
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    if case == "batch":
+        batch = synth.batch(0, N_IMAGES, workers=min(16, os.cpu_count() or 1))
+        dev_in, dev_out, _, _, offs = upload_batch(batch, device)
+        descs = descs_for(_lib, batch, dev_in, dev_out, offs)
+        for _ in range(launches):
+            _lib.check(lib.me_edges_batch(descs, len(batch), stream.cuda_stream))
+        torch.cuda.synchronize()
+        ok, n = verify_sample(batch, dev_out, offs)
+    else:
+        w = h = 32768
+        words = synth.bernoulli_half_packed(w, h, seed=0)
+        x = torch.from_numpy(words.view(np.int32)).to(device)
+        y = torch.empty_like(x)
+        for _ in range(launches):
+            _lib.check(lib.me_edges(x.data_ptr(), w, h, 1024, y.data_ptr(), 0,
+                                    stream.cuda_stream))
+        torch.cuda.synchronize()
+        ok = True
+    print(json.dumps({"profile_case": case, "launches": launches, "exact": ok}))
+    return 0 if ok else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile", choices=["batch", "single"], default=None,
+                    help="run a few launches of one kernel for an ncu capture")
+    ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--cfg", default=None, help="tile configuration for --profile")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
@@ -475,6 +517,8 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args(argv)
     rank, world, local_rank = rank_info()
+    if args.profile:
+        return run_profile_case(args.profile, args.launches, args.cfg)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_ours(args, rank, world, local_rank)

@@ -228,11 +228,15 @@ int me_batch_plan_destroy(me_batch_plan *plan);
 
 typedef struct me_tile_cfg {
     int32_t engine;          /* ME_ENGINE_REGS or ME_ENGINE_BULK */
-    int32_t rows_per_lane;   /* rows one lane walks: 4, 8, 16 or 32 */
-    int32_t vec_words;       /* 4: 128-bit loads where aligned; 1: 32-bit */
+    int32_t rows_per_lane;   /* REGS: rows one lane walks: 4, 8, 16 or 32 */
+    int32_t vec_words;       /* REGS: 4 = 128-bit loads where aligned, 1 = 32-bit */
     int32_t cta_threads;     /* 128, 256 or 512 */
-    int32_t ctas_per_sm;     /* persistent grid of SMs x this; 0 = one warp
-                                per tile, no persistence */
+    int32_t ctas_per_sm;     /* persistent grid of SMs x this, capped by what
+                                fits on an SM; 0 = REGS: one warp per tile,
+                                BULK: as many as fit */
+    int32_t stage_kb;        /* BULK: KiB per shared-memory stage (4..64) */
+    int32_t stages;          /* BULK: stages in the ring (2..8); stages x
+                                stage_kb <= 216 */
 } me_tile_cfg;
 
 /* Read or replace the configuration used by the calls of `kind`. */
@@ -318,6 +322,14 @@ int me_serve_stats(me_server *srv, int64_t *submitted, int64_t *completed,
  * out (the server is freed all the same once its GPU work has ended).
  */
 int me_serve_close(me_server *srv, int64_t drain_timeout_us);
+
+/*
+ * Bounded waits that ran out in library kernels since the last clear, as
+ * a bit set (0 in a healthy run; bit 0: a bulk-copy stage never arrived, the
+ * kernel stopped early and its outputs are incomplete).  clear != 0 resets
+ * it.  Synchronises with the current device.
+ */
+int me_device_faults(int32_t clear, uint32_t *flags);
 
 /* Free the batch rings, graphs and plans' shared state on every device. */
 int me_shutdown(void);

@@ -54,7 +54,8 @@ class me_desc(ctypes.Structure):
 
 class me_tile_cfg(ctypes.Structure):
     _fields_ = [("engine", c_i32), ("rows_per_lane", c_i32), ("vec_words", c_i32),
-                ("cta_threads", c_i32), ("ctas_per_sm", c_i32)]
+                ("cta_threads", c_i32), ("ctas_per_sm", c_i32), ("stage_kb", c_i32),
+                ("stages", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,6 +102,7 @@ PROTOTYPES = {
     "me_serve_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                                       ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     "me_serve_close": (ctypes.c_int, [c_vp, c_i64]),
+    "me_device_faults": (ctypes.c_int, [c_i32, ctypes.POINTER(ctypes.c_uint32)]),
     "me_shutdown": (ctypes.c_int, []),
 }
 
@@ -245,6 +247,12 @@ def me_autotune(kind, descs, n=None, reps=10, stream=None) -> me_tile_cfg:
     check(load().me_autotune(kind, descs, n, reps, stream_handle(stream),
                              ctypes.byref(best)), "me_autotune")
     return best
+
+
+def me_device_faults(clear=True) -> int:
+    v = ctypes.c_uint32()
+    check(load().me_device_faults(1 if clear else 0, ctypes.byref(v)), "me_device_faults")
+    return v.value
 
 
 def me_shutdown() -> int:

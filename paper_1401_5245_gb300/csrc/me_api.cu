@@ -102,8 +102,8 @@ Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
 // ------------------------------------------------------------ tile configs
 static std::mutex g_cfg_mu;
 static me_tile_cfg g_cfg[2] = {
-    {ME_ENGINE_REGS, 8, 4, 256, 0},     // single image
-    {ME_ENGINE_REGS, 8, 4, 256, 4},     // batch
+    {ME_ENGINE_REGS, 8, 4, 256, 0, 32, 4},     // single image
+    {ME_ENGINE_REGS, 8, 4, 256, 4, 32, 4},     // batch
 };
 
 void apply_tune_cache(int kind);
@@ -120,13 +120,17 @@ bool valid_cfg(const me_tile_cfg &c) {
     const bool vec = c.vec_words == 1 || c.vec_words == 4;
     const bool thr = c.cta_threads == 128 || c.cta_threads == 256 || c.cta_threads == 512;
     const bool eng = c.engine == ME_ENGINE_REGS || c.engine == ME_ENGINE_BULK;
-    return rows && vec && thr && eng && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
+    const bool stage = c.stage_kb >= 4 && c.stage_kb <= 64 && c.stages >= 2 && c.stages <= 8 &&
+                       c.stage_kb * c.stages <= 216;
+    return rows && vec && thr && eng && stage && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
 }
 
 uint64_t cfg_key(const me_tile_cfg &c) {
-    return ((uint64_t)c.engine << 40) | ((uint64_t)c.rows_per_lane << 32) |
-           ((uint64_t)c.vec_words << 24) | ((uint64_t)c.cta_threads << 8) |
-           (uint64_t)c.ctas_per_sm;
+    uint64_t k = (uint64_t)c.engine;
+    for (int32_t v : {c.rows_per_lane, c.vec_words, c.cta_threads, c.ctas_per_sm, c.stage_kb,
+                      c.stages})
+        k = k * 1000003ull + (uint64_t)v;
+    return k;
 }
 
 }  // namespace me
@@ -162,6 +166,14 @@ int me_last_cuda_error(void) {
 
 int me_version(void) { return 10000; }
 
+int me_device_faults(int32_t clear, uint32_t *flags) {
+    if (flags == nullptr) return ME_ERR_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return record_cuda(e);
+    *flags = device_fault_flags(clear != 0);
+    return ME_OK;
+}
+
 int me_get_tile_cfg(int32_t kind, me_tile_cfg *out) {
     if (out == nullptr || (kind != ME_KIND_SINGLE && kind != ME_KIND_BATCH)) return ME_ERR_ARG;
     *out = tile_cfg(kind);
@@ -171,7 +183,6 @@ int me_get_tile_cfg(int32_t kind, me_tile_cfg *out) {
 int me_set_tile_cfg(int32_t kind, const me_tile_cfg *cfg) {
     if (cfg == nullptr || (kind != ME_KIND_SINGLE && kind != ME_KIND_BATCH)) return ME_ERR_ARG;
     if (!valid_cfg(*cfg)) return ME_ERR_ARG;
-    if (kind == ME_KIND_BATCH && cfg->engine != ME_ENGINE_REGS) return ME_ERR_UNSUPPORTED;
     if (cfg->engine == ME_ENGINE_BULK && !bulk_available()) return ME_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_cfg_mu);
     g_cfg[kind] = *cfg;
@@ -190,7 +201,7 @@ static int single_call(int mode, const uint32_t *img, int32_t w, int32_t h,
     const Geo g = make_geo(img, w, h, stride_words, boundary,
                            pick_vw(img, out, stride_words, cfg.vec_words));
     cudaError_t e;
-    if (mode == MODE_EDGE && cfg.engine == ME_ENGINE_BULK && bulk_eligible(g, out)) {
+    if (mode == MODE_EDGE && cfg.engine == ME_ENGINE_BULK) {
         e = launch_bulk(g, out, cfg, (cudaStream_t)stream);
     } else {
         Outs o = {{out, nullptr, nullptr, nullptr}};

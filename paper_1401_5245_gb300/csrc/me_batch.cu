@@ -1,14 +1,15 @@
 // me_edges_batch and batch plans: many images in one persistent launch,
 // replayed from CUDA graphs.
 //
-// A call plans the batch on the host (descriptors, tile ranges per warp),
-// writes the plan into a pinned staging slot and launches that slot's
-// graph: one memcpy node (staging -> device arena) and one kernel node (the
-// persistent batch kernel reading the arena).  Slots form a ring of
-// kRing per device; a slot is reused only after the event recorded behind
-// its last launch has completed, so in-flight graphs never see their
-// staging or arena overwritten.  Graphs are cached per slot and keyed by the
-// tile configuration and grid; the memcpy node's size is set per launch.
+// A call plans the batch on the host (descriptors, each work owner's first
+// image), writes the plan into a pinned staging slot and launches that
+// slot's graph: one memcpy node (staging -> device arena) and one kernel
+// node (the persistent batch kernel of the configured engine reading the
+// arena).  Slots form a ring of kRing per device; a slot is reused only
+// after the event recorded behind its last launch has completed, so graphs
+// in flight never see their staging or arena overwritten.  Graphs are
+// cached per slot, keyed by the tile configuration and grid; the memcpy
+// node's size is set per launch.
 #include <algorithm>
 #include <cstring>
 #include <memory>
@@ -80,26 +81,86 @@ size_t round_pow2(size_t v) {
     return c;
 }
 
-// Graph: copy `cap` bytes host -> arena, then the persistent kernel.
-cudaError_t build_graph(const void *host, void *dev, size_t bytes, int grid,
-                        int threads, int rpt, GraphEntry *out) {
+int fail(cudaError_t e) {
+    cudaGetLastError();
+    return record_cuda(e);
+}
+
+// How one batch launches under a configuration.
+struct Setup {
+    me_tile_cfg cfg;
+    int grid = 0, threads = 0;
+    size_t smem = 0, arena = 0;
+    const void *fn = nullptr;
+    int stage_words = 0;
+};
+
+int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, Setup *s) {
+    int64_t units = 0;
+    int rc;
+    s->cfg = cfg;
+    if (cfg.engine == ME_ENGINE_BULK) {
+        if ((rc = batch_bands(descs, n, cfg, &units)) != ME_OK) return rc;
+    } else {
+        if ((rc = batch_tasks(descs, n, cfg, &units)) != ME_OK) return rc;
+    }
+    DevInfo di;
+    if ((rc = device_info(&di)) != ME_OK) return rc;
+    if (cfg.engine == ME_ENGINE_BULK) {
+        int occ = 0;
+        if ((rc = bulk_ctas_per_sm(cfg, &occ)) != ME_OK) return rc;
+        if (occ < 1) return ME_ERR_ARG;
+        const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
+        s->grid = di.sm_count * per_sm;
+        s->threads = cfg.cta_threads;
+        s->smem = bulk_smem_bytes(cfg);
+        s->stage_words = (int)(s->smem / cfg.stages / 4);
+        s->arena = bulk_arena_bytes(n, s->grid);
+        s->fn = bulk_kernel();
+    } else {
+        if ((rc = batch_grid(cfg, di, &s->grid, &s->threads)) != ME_OK) return rc;
+        s->arena = arena_bytes(n, s->grid * (s->threads / 32));
+        s->fn = batch_kernel(cfg.rows_per_lane);
+    }
+    return ME_OK;
+}
+
+int fill_arena(const me_desc *descs, int n, const Setup &s, void *host) {
+    if (s.cfg.engine == ME_ENGINE_BULK) {
+        int64_t bands = 0;
+        return plan_batch_bulk(descs, n, s.cfg, s.grid, host, &bands);
+    }
+    int bad = -1;
+    return plan_batch(descs, n, s.cfg, s.grid * (s.threads / 32), host, &bad);
+}
+
+// Kernel node of the batch kernel reading the arena at `dev`.
+cudaError_t add_kernel_node(cudaGraph_t g, const cudaGraphNode_t *dep, size_t ndep,
+                            const Setup &s, void *dev, cudaGraphNode_t *node) {
+    cudaKernelNodeParams kp = {};
+    void *arena = dev;
+    KDescB none = {};
+    int zero = 0, stage_words = s.stage_words, stages = s.cfg.stages;
+    void *regs_args[] = {&arena};
+    void *bulk_args[] = {&arena, &none, &zero, &stage_words, &stages};
+    kp.func = const_cast<void *>(s.fn);
+    kp.gridDim = dim3(s.grid);
+    kp.blockDim = dim3(s.threads);
+    kp.sharedMemBytes = (unsigned)s.smem;
+    kp.kernelParams = s.cfg.engine == ME_ENGINE_BULK ? bulk_args : regs_args;
+    return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
+}
+
+// Graph: copy the arena host -> device, then the persistent kernel.
+cudaError_t build_graph(const void *host, void *dev, size_t bytes, const Setup &s,
+                        GraphEntry *out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return e;
     cudaGraphNode_t copy = nullptr, kern = nullptr;
     e = cudaGraphAddMemcpyNode1D(&copy, g, nullptr, 0, dev, host, bytes,
                                  cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        cudaKernelNodeParams kp = {};
-        void *arena = dev;
-        void *args[] = {&arena};
-        kp.func = const_cast<void *>(batch_kernel(rpt));
-        kp.gridDim = dim3(grid);
-        kp.blockDim = dim3(threads);
-        kp.sharedMemBytes = 0;
-        kp.kernelParams = args;
-        e = cudaGraphAddKernelNode(&kern, g, &copy, 1, &kp);
-    }
+    if (e == cudaSuccess) e = add_kernel_node(g, &copy, 1, s, dev, &kern);
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
     if (e != cudaSuccess) {
@@ -110,11 +171,6 @@ cudaError_t build_graph(const void *host, void *dev, size_t bytes, int grid,
     out->exec = exec;
     out->copy = copy;
     return cudaSuccess;
-}
-
-int fail(cudaError_t e) {
-    cudaGetLastError();
-    return record_cuda(e);
 }
 
 }  // namespace
@@ -155,17 +211,9 @@ extern "C" {
 int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream) {
     if (n < 0 || (n > 0 && descs == nullptr)) return ME_ERR_ARG;
     if (n == 0) return ME_OK;
-    me_tile_cfg cfg = tile_cfg(ME_KIND_BATCH);
-    if (cfg.ctas_per_sm <= 0) cfg.ctas_per_sm = 4;
-    int64_t tasks = 0;
-    int rc = batch_tasks(descs, n, cfg, &tasks);
+    Setup su;
+    int rc = setup_batch(descs, n, tile_cfg(ME_KIND_BATCH), &su);
     if (rc != ME_OK) return rc;
-    DevInfo di;
-    if ((rc = device_info(&di)) != ME_OK) return rc;
-    int grid = 0, threads = 0;
-    batch_grid(cfg, di, (int)tasks, &grid, &threads);
-    const int total_warps = grid * (threads / 32);
-    const size_t need = arena_bytes(n, total_warps);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -179,9 +227,9 @@ int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream) {
         if (e != cudaSuccess) return fail(e);
         slot.pending = false;
     }
-    if (slot.cap < need) {
+    if (slot.cap < su.arena) {
         slot.release();
-        const size_t cap = round_pow2(need);
+        const size_t cap = round_pow2(su.arena);
         if ((e = cudaHostAlloc(&slot.host, cap, cudaHostAllocDefault)) != cudaSuccess) {
             slot.host = nullptr;
             return fail(e);
@@ -198,21 +246,19 @@ int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream) {
         }
         slot.cap = cap;
     }
-    int bad = -1;
-    if ((rc = plan_batch(descs, n, cfg, total_warps, slot.host, &bad)) != ME_OK) return rc;
+    if ((rc = fill_arena(descs, n, su, slot.host)) != ME_OK) return rc;
 
-    const uint64_t key = cfg_key(cfg) ^ ((uint64_t)grid << 44);
+    const uint64_t key = cfg_key(su.cfg) * 31 + (uint64_t)su.grid;
     auto it = slot.graphs.find(key);
     if (it == slot.graphs.end()) {
         GraphEntry ge;
-        if ((e = build_graph(slot.host, slot.dev, slot.cap, grid, threads,
-                             cfg.rows_per_lane, &ge)) != cudaSuccess)
+        if ((e = build_graph(slot.host, slot.dev, slot.cap, su, &ge)) != cudaSuccess)
             return fail(e);
         it = slot.graphs.emplace(key, ge).first;
     }
     // copy only what this batch filled
     e = cudaGraphExecMemcpyNodeSetParams1D(it->second.exec, it->second.copy, slot.dev,
-                                           slot.host, need, cudaMemcpyHostToDevice);
+                                           slot.host, su.arena, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(e);
     if ((e = cudaGraphLaunch(it->second.exec, (cudaStream_t)stream)) != cudaSuccess)
         return fail(e);
@@ -225,47 +271,30 @@ int me_batch_plan_create(const me_desc *descs, int32_t n, me_stream_t stream,
                          me_batch_plan **out) {
     if (out == nullptr || n <= 0 || descs == nullptr) return ME_ERR_ARG;
     *out = nullptr;
-    me_tile_cfg cfg = tile_cfg(ME_KIND_BATCH);
-    if (cfg.ctas_per_sm <= 0) cfg.ctas_per_sm = 4;
-    int64_t tasks = 0;
-    int rc = batch_tasks(descs, n, cfg, &tasks);
+    Setup su;
+    int rc = setup_batch(descs, n, tile_cfg(ME_KIND_BATCH), &su);
     if (rc != ME_OK) return rc;
-    DevInfo di;
-    if ((rc = device_info(&di)) != ME_OK) return rc;
-    int grid = 0, threads = 0;
-    batch_grid(cfg, di, (int)tasks, &grid, &threads);
-    const int total_warps = grid * (threads / 32);
-    const size_t need = arena_bytes(n, total_warps);
     std::vector<unsigned char> host;
     try {
-        host.resize(need);
+        host.resize(su.arena);
     } catch (...) {
         return ME_ERR_NOMEM;
     }
-    if ((rc = plan_batch(descs, n, cfg, total_warps, host.data(), nullptr)) != ME_OK) return rc;
+    if ((rc = fill_arena(descs, n, su, host.data())) != ME_OK) return rc;
 
     std::unique_ptr<me_batch_plan> p(new (std::nothrow) me_batch_plan());
     if (!p) return ME_ERR_NOMEM;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&p->dev, need)) != cudaSuccess) return fail(e);
-    p->bytes = need;
+    if ((e = cudaMalloc(&p->dev, su.arena)) != cudaSuccess) return fail(e);
+    p->bytes = su.arena;
     p->algo_bytes = reinterpret_cast<BatchHeader *>(host.data())->bytes;
-    e = cudaMemcpyAsync(p->dev, host.data(), need, cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(p->dev, host.data(), su.arena, cudaMemcpyHostToDevice,
                         (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaGraphCreate(&p->graph, 0);
-    if (e == cudaSuccess) {
-        cudaKernelNodeParams kp = {};
-        void *arena = p->dev;
-        void *args[] = {&arena};
-        kp.func = const_cast<void *>(batch_kernel(cfg.rows_per_lane));
-        kp.gridDim = dim3(grid);
-        kp.blockDim = dim3(threads);
-        kp.kernelParams = args;
-        cudaGraphNode_t node;
-        e = cudaGraphAddKernelNode(&node, p->graph, nullptr, 0, &kp);
-    }
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = add_kernel_node(p->graph, nullptr, 0, su, p->dev, &node);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
     if (e != cudaSuccess) {
         me_batch_plan_destroy(p.release());
@@ -295,6 +324,6 @@ int me_batch_plan_destroy(me_batch_plan *plan) {
     return ME_OK;
 }
 
-}  // extern "C"
+int me_shutdown(void) { return batch_shutdown_all(); }
 
-extern "C" int me_shutdown(void) { return me::batch_shutdown_all(); }
+}  // extern "C"

@@ -48,6 +48,26 @@ struct BDesc {
 };
 static_assert(sizeof(BDesc) == 64, "BDesc is 64 bytes");
 
+// Image descriptor of the bulk-copy engine (64 bytes).  The image is cut
+// into bands of band_rows rows x band_words words; a band plus one halo row
+// above and below (and 4 halo words left and right in column mode) is
+// copied into one shared-memory stage laid out as rows of `pitch` words,
+// stage column 0 holding image word x0 - xhalo.
+struct KDescB {
+    const uint32_t *img;
+    uint32_t *edge;
+    int32_t flags;              // kBulkCopy | kVecStore | kRowMode
+    int32_t h, stride, nw;
+    uint32_t lastmask, fill;
+    int32_t band_rows, band_words, pitch;
+    int32_t ncb, nrb;           // column blocks, row bands
+    int32_t band_base;          // first band of this image in the batch
+};
+static_assert(sizeof(KDescB) == 64, "KDescB is 64 bytes");
+constexpr int32_t kBulkCopy = 1;    // copy with cp.async.bulk (16-byte rows)
+constexpr int32_t kVecStore = 2;    // 128-bit stores allowed
+constexpr int32_t kRowMode = 4;     // full rows, one contiguous copy per band
+
 // Device arena of one batch: header, then descriptors, then the first task
 // of every warp's contiguous task range.
 struct BatchHeader {
@@ -94,20 +114,33 @@ uint64_t cfg_key(const me_tile_cfg &c);
 // Single image, register-window engine.  `launches` counts kernels issued.
 cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
                           const me_tile_cfg &cfg, cudaStream_t s);
-// Single image, bulk-copy (TMA) engine; only MODE_EDGE.  Returns
-// cudaErrorNotSupported when the image does not meet the engine's
-// alignment rules (caller falls back).
+// Single image, bulk-copy (TMA) engine; MODE_EDGE only.
 cudaError_t launch_bulk(const Geo &g, uint32_t *edge, const me_tile_cfg &cfg,
                         cudaStream_t s);
-bool bulk_eligible(const Geo &g, const void *edge);
 bool bulk_available();
+// Band geometry of one image for a stage of stage_words words.
+void bulk_geometry(const Geo &g, const void *edge, int stage_words, KDescB *out);
+// Persistent bulk kernel: function pointer, dynamic shared memory, and the
+// CTAs per SM it can keep resident (after raising its smem limit).
+const void *bulk_kernel();
+size_t bulk_smem_bytes(const me_tile_cfg &cfg);
+int bulk_ctas_per_sm(const me_tile_cfg &cfg, int *out);
+int regs_ctas_per_sm(const void *fn, int threads, int *out);
+// Host plan of a bulk batch arena (header, KDescB[n], first image per CTA).
+int plan_batch_bulk(const me_desc *descs, int n, const me_tile_cfg &cfg, int grid,
+                    void *host_arena, int64_t *total_bands);
+int batch_bands(const me_desc *descs, int n, const me_tile_cfg &cfg, int64_t *total);
+inline size_t bulk_arena_bytes(int n, int grid) {
+    return sizeof(BatchHeader) + (size_t)n * sizeof(KDescB) +
+           (((size_t)grid + 1) * sizeof(int32_t) + 255) / 256 * 256;
+}
+unsigned int device_fault_flags(bool clear);
 
 // Persistent batch kernel over an uploaded arena.
 cudaError_t launch_batch(const void *arena_dev, int grid, int threads,
                          int rows_per_lane, cudaStream_t s);
 const void *batch_kernel(int rows_per_lane);   // for graph kernel nodes
-void batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int total_tasks,
-                int *grid, int *threads);
+int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int *grid, int *threads);
 
 // Fill descriptors and the warp start table of a batch arena on the host.
 // Returns ME_OK or an argument error for descriptor i (*bad = i).

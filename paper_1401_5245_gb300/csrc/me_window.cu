@@ -67,7 +67,11 @@ cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
     if (cfg.ctas_per_sm > 0) {
         DevInfo di;
         if (device_info(&di) != ME_OK) return cudaErrorInvalidDevice;
-        grid = std::min<int64_t>(grid, (int64_t)di.sm_count * cfg.ctas_per_sm);
+        int occ = 0;
+        if (regs_ctas_per_sm(reinterpret_cast<const void *>(fn), threads, &occ) != ME_OK)
+            return cudaErrorInvalidValue;
+        const int per_sm = std::max(1, std::min(cfg.ctas_per_sm, occ));
+        grid = std::min<int64_t>(grid, (int64_t)di.sm_count * per_sm);
     }
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, INT32_MAX));
     fn<<<(unsigned)grid, threads, 0, s>>>(g, o, (int)ntasks);
@@ -133,16 +137,26 @@ static BatchFn pick_batch(int rpt) {
     }
 }
 
-void batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int total_tasks,
-                int *grid, int *threads) {
-    const int warps_per_cta = cfg.cta_threads / 32;
-    int64_t g;
-    if (cfg.ctas_per_sm > 0)
-        g = (int64_t)di.sm_count * cfg.ctas_per_sm;
-    else
-        g = ((int64_t)total_tasks + warps_per_cta - 1) / warps_per_cta;
-    *grid = (int)std::max<int64_t>(1, std::min<int64_t>(g, 1 << 20));
+int regs_ctas_per_sm(const void *fn, int threads, int *out) {
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return record_cuda(e);
+    }
+    *out = n;
+    return ME_OK;
+}
+
+int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int *grid, int *threads) {
+    int occ = 0;
+    int rc = regs_ctas_per_sm(reinterpret_cast<const void *>(pick_batch(cfg.rows_per_lane)),
+                              cfg.cta_threads, &occ);
+    if (rc != ME_OK) return rc;
+    const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ, occ));
+    *grid = di.sm_count * per_sm;
     *threads = cfg.cta_threads;
+    return ME_OK;
 }
 
 cudaError_t launch_batch(const void *arena_dev, int grid, int threads,

@@ -4,10 +4,16 @@
 // (VW = 4: one 128-bit load per lane and row; VW = 1: one 32-bit load).
 // Narrow images fold the warp: a row segment uses nvp = 2^seg_log2 lanes
 // and the warp stacks 32 / nvp segments vertically, so every lane has work
-// whatever the width.  Each lane loads its rows y0-1 .. y0+RPT once into
-// registers, takes the horizontal neighbour words from the lanes beside it
-// with shuffles (lanes at a segment end load the one word beyond, or use
-// the outside colour), and writes RPT output words.
+// whatever the width.  Each lane streams its RPT rows top to bottom: the
+// rows above, at and below the output row sit in registers, the next
+// kPrefetch rows are already requested, so each input word is loaded once
+// and kPrefetch + 3 rows are live per lane.  Horizontal neighbour words come
+// from the lanes beside it by shuffles; a lane at a segment end loads the
+// one word beyond it, or uses the outside colour.
+//
+// Outside the image (rows, words, padding bits) reads as the boundary
+// colour.  Per lane the fix-up of its VW words is precomputed as two masks,
+// applied with one three-input logic op per word: fixed = (raw & keep) | fb.
 //
 // Word form of the paper's steps, least significant bit = leftmost pixel:
 //   mask          M = ~I                                    (Section 3)
@@ -24,66 +30,20 @@
 
 namespace me {
 
+// Rows requested ahead of the one being computed; RPT is a multiple of it.
+constexpr int kPrefetch = 4;
+
 template <int VW>
 struct Words {
     uint32_t v[VW];
 };
 
-// Word c of row y with the outside colour applied: rows and words outside
-// the image read as `fill`, the padding bits of word nw-1 as well.
-__device__ __forceinline__ uint32_t fix_word(const Geo &g, int c, uint32_t x) {
-    if (c >= g.nw) return g.fill;
-    if (c == g.nw - 1) return (x & g.lastmask) | (g.fill & ~g.lastmask);
-    return x;
-}
-
+// A row as a lane holds it: its VW words and the words just outside them.
 template <int VW>
-__device__ __forceinline__ Words<VW> load_row(const Geo &g, int y, int c0) {
-    Words<VW> r;
-    if ((unsigned)y < (unsigned)g.h && c0 < g.nw) {
-        const uint32_t *p = g.img + (size_t)y * (size_t)g.stride + c0;
-        if constexpr (VW == 4) {
-            // 16-byte aligned: img is, stride % 4 == 0 and c0 % 4 == 0; the
-            // four words stay inside the row's stride.
-            uint4 q = __ldg(reinterpret_cast<const uint4 *>(p));
-            r.v[0] = fix_word(g, c0 + 0, q.x);
-            r.v[1] = fix_word(g, c0 + 1, q.y);
-            r.v[2] = fix_word(g, c0 + 2, q.z);
-            r.v[3] = fix_word(g, c0 + 3, q.w);
-        } else {
-            r.v[0] = fix_word(g, c0, __ldg(p));
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < VW; ++k) r.v[k] = g.fill;
-    }
-    return r;
-}
-
-// Single word c of row y (outside colour applied); for the halo lanes.
-__device__ __forceinline__ uint32_t load_word(const Geo &g, int y, int c) {
-    if ((unsigned)y < (unsigned)g.h && c >= 0 && c < g.nw)
-        return fix_word(g, c, __ldg(g.img + (size_t)y * (size_t)g.stride + c));
-    return g.fill;
-}
-
-template <int VW>
-__device__ __forceinline__ void store_row(const Geo &g, uint32_t *out, int y,
-                                          int c0, const Words<VW> &e) {
-    if (y >= g.h || c0 >= g.nw || out == nullptr) return;
-    uint32_t *p = out + (size_t)y * (size_t)g.stride + c0;
-    if constexpr (VW == 4) {
-        if (c0 + 3 < g.nw) {
-            __stcs(reinterpret_cast<uint4 *>(p), make_uint4(e.v[0], e.v[1], e.v[2], e.v[3]));
-            return;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (c0 + k < g.nw) __stcs(p + k, e.v[k]);
-    } else {
-        __stcs(p, e.v[0]);
-    }
-}
+struct Row {
+    Words<VW> w;
+    uint32_t hl, hr;          // raw halo words of segment-end lanes
+};
 
 // Image moved one pixel right: bit x holds pixel x-1.
 __device__ __forceinline__ uint32_t from_left(uint32_t prev, uint32_t cur) {
@@ -94,113 +54,222 @@ __device__ __forceinline__ uint32_t from_right(uint32_t cur, uint32_t next) {
     return __funnelshift_r(cur, next, 1);
 }
 
-// Rows loaded ahead of the one being computed.
-constexpr int kPrefetch = 4;
+// Per-lane constants of one tile.
+template <int VW>
+struct Lane {
+    const uint32_t *base;      // image word c0 of row 0
+    uint32_t *out[4];          // output word c0 of row 0, per output
+    int stride, h, nw, nvp, c0;
+    uint32_t fill;
+    uint32_t keep[VW], fb[VW]; // fixed = (raw & keep) | fb
+    uint32_t nkeep, nfb;       // the same for the word after the lane
+    bool active;               // c0 < nw
+    bool seg_first, seg_last, has_prev, has_next;
+};
 
-// One warp tile: column block cb, row block rb of image g.  Rows stream
-// through a register window: row r+kPrefetch is requested while row r is
-// computed, so at most kPrefetch + 2 rows are live per lane.
-template <int VW, int RPT, int MODE>
-__device__ __forceinline__ void window_tile(const Geo &g, const Outs &o, int cb,
-                                            int rb, int lane) {
+template <int VW>
+__device__ __forceinline__ uint32_t col_keep(const Geo &g, int c) {
+    return c < g.nw - 1 ? kAllOnes : (c == g.nw - 1 ? g.lastmask : 0u);
+}
+
+template <int VW>
+__device__ __forceinline__ Lane<VW> make_lane(const Geo &g, const Outs &o, int c0, int col,
+                                              int nvp) {
+    Lane<VW> L;
+    L.base = g.img + c0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) L.out[k] = o.p[k] ? o.p[k] + c0 : nullptr;
+    L.stride = g.stride;
+    L.h = g.h;
+    L.nw = g.nw;
+    L.nvp = nvp;
+    L.c0 = c0;
+    L.fill = g.fill;
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {
+        L.keep[k] = col_keep<VW>(g, c0 + k);
+        L.fb[k] = g.fill & ~L.keep[k];
+    }
+    L.nkeep = col_keep<VW>(g, c0 + VW);
+    L.nfb = g.fill & ~L.nkeep;
+    L.active = c0 < g.nw;
+    L.seg_first = (col == 0);
+    L.seg_last = (col == nvp - 1);
+    L.has_prev = L.seg_first && L.active && c0 > 0;
+    L.has_next = L.seg_last && (c0 + VW < g.nw);
+    return L;
+}
+
+// Row y into registers.  CHECK: y may lie outside [0, h).
+template <int VW, bool CHECK>
+__device__ __forceinline__ Row<VW> load_row(const Lane<VW> &L, int y) {
+    Row<VW> r;
+    const bool ok = L.active && (!CHECK || (unsigned)y < (unsigned)L.h);
+    const uint32_t *p = L.base + (size_t)y * (size_t)L.stride;
+    uint32_t raw[VW];
+    if constexpr (VW == 4) {
+        uint4 q = make_uint4(0, 0, 0, 0);
+        // 16-byte aligned: img is, stride % 4 == 0 and c0 % 4 == 0; the four
+        // words stay inside the row's stride.
+        if (ok) q = __ldg(reinterpret_cast<const uint4 *>(p));
+        raw[0] = q.x; raw[1] = q.y; raw[2] = q.z; raw[3] = q.w;
+    } else {
+        raw[0] = ok ? __ldg(p) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {
+        const uint32_t f = (raw[k] & L.keep[k]) | L.fb[k];
+        r.w.v[k] = (!CHECK || ok || !L.active) ? f : L.fill;
+    }
+    const bool rowok = !CHECK || (unsigned)y < (unsigned)L.h;
+    r.hl = (L.has_prev && rowok) ? __ldg(p - 1) : L.fill;
+    r.hr = (L.has_next && rowok) ? ((__ldg(p + VW) & L.nkeep) | L.nfb) : L.fill;
+    return r;
+}
+
+// Words just left and right of the lane's VW words in row r.
+template <int VW>
+__device__ __forceinline__ void side_words(const Lane<VW> &L, const Row<VW> &r, uint32_t &prev,
+                                           uint32_t &next) {
+    const uint32_t a = __shfl_up_sync(0xFFFFFFFFu, r.w.v[VW - 1], 1, L.nvp);
+    const uint32_t b = __shfl_down_sync(0xFFFFFFFFu, r.w.v[0], 1, L.nvp);
+    prev = L.seg_first ? r.hl : a;
+    next = L.seg_last ? r.hr : b;
+}
+
+template <int VW>
+__device__ __forceinline__ void store_words(const Lane<VW> &L, uint32_t *out, int y,
+                                            const uint32_t (&e)[VW]) {
+    uint32_t *p = out + (size_t)y * (size_t)L.stride;
+    if constexpr (VW == 4) {
+        if (L.c0 + 3 < L.nw) {
+            __stcs(reinterpret_cast<uint4 *>(p), make_uint4(e[0], e[1], e[2], e[3]));
+            return;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (L.c0 + k < L.nw) __stcs(p + k, e[k]);
+    } else {
+        __stcs(p, e[0]);
+    }
+}
+
+// One output row from the rows above (u), at (c) and below (d).
+template <int VW, int MODE>
+__device__ __forceinline__ void emit_row(const Lane<VW> &L, int y, const Row<VW> &u,
+                                         const Row<VW> &c, const Row<VW> &d, uint32_t cp,
+                                         uint32_t cn, uint32_t up_p, uint32_t up_n,
+                                         uint32_t dn_p, uint32_t dn_n) {
+    uint32_t e0[VW], e1[VW], e2[VW], e3[VW];
+#pragma unroll
+    for (int k = 0; k < VW; ++k) {
+        const uint32_t cur = c.w.v[k];
+        const uint32_t pv = (k == 0) ? cp : c.w.v[k - 1];
+        const uint32_t nx = (k == VW - 1) ? cn : c.w.v[k + 1];
+        const uint32_t Lw = from_left(pv, cur);         // I(x-1, y)
+        const uint32_t Rw = from_right(cur, nx);        // I(x+1, y)
+        const uint32_t U = u.w.v[k];                    // I(x, y-1)
+        const uint32_t D = d.w.v[k];                    // I(x, y+1)
+        const uint32_t M = ~cur;                        // the mask
+        const uint32_t valid = L.keep[k];
+        if constexpr (MODE == MODE_EDGE) {
+            e0[k] = M & (Lw | Rw | U | D) & valid;
+        } else if constexpr (MODE == MODE_DISPLAY) {
+            e0[k] = ~(M & (Lw | Rw | U | D)) & valid;
+        } else if constexpr (MODE == MODE_FUND) {
+            e0[k] = M & Lw & valid;
+            e1[k] = M & Rw & valid;
+            e2[k] = M & U & valid;
+            e3[k] = M & D & valid;
+        } else {
+            // Fig. 1 neighbours 1..8 of every pixel of the word, as "is
+            // white" planes; count the black ones bit-sliced and keep
+            // pixels with at most one.
+            const uint32_t pu = (k == 0) ? up_p : u.w.v[k - 1];
+            const uint32_t nu = (k == VW - 1) ? up_n : u.w.v[k + 1];
+            const uint32_t pd = (k == 0) ? dn_p : d.w.v[k - 1];
+            const uint32_t nd = (k == VW - 1) ? dn_n : d.w.v[k + 1];
+            const uint32_t nb[8] = {
+                from_right(U, nu),   // 1: up-right
+                U,                   // 2: up
+                from_left(pu, U),    // 3: up-left
+                Lw,                  // 4: left
+                from_left(pd, D),    // 5: down-left
+                D,                   // 6: down
+                from_right(D, nd),   // 7: down-right
+                Rw                   // 8: right
+            };
+            uint32_t one = 0, two = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t black = ~nb[j];
+                two |= one & black;
+                one |= black;
+            }
+            e0[k] = M & ~two & valid;
+        }
+    }
+    store_words<VW>(L, L.out[0], y, e0);
+    if constexpr (MODE == MODE_FUND) {
+        store_words<VW>(L, L.out[1], y, e1);
+        store_words<VW>(L, L.out[2], y, e2);
+        store_words<VW>(L, L.out[3], y, e3);
+    }
+}
+
+// One warp tile: column block cb, row block rb of image g.  CHECK: the
+// tile's rows, with one halo row above and below, may leave the image.
+template <int VW, int RPT, int MODE, bool CHECK>
+__device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, int cb, int rb,
+                                                 int lane) {
+    static_assert(RPT % kPrefetch == 0, "rows per lane is a multiple of the prefetch");
     const int nvp = 1 << g.seg_log2;
     const int col = lane & (nvp - 1);
     const int seg = lane >> g.seg_log2;
-    const int v = cb * 32 + col;
-    const int c0 = v * VW;
+    const int c0 = (cb * 32 + col) * VW;
     const int y0 = ((rb << (5 - g.seg_log2)) + seg) * RPT;
-    const bool seg_first = (col == 0);
-    const bool seg_last = (col == nvp - 1);
+    const Lane<VW> L = make_lane<VW>(g, o, c0, col, nvp);
+    const bool rows_left = !CHECK || y0 < g.h;    // segment has rows (uniform per segment)
 
-    // window index r holds row y0 - 1 + r, r = 0 .. RPT + 1
-    Words<VW> win[RPT + 2];
-    uint32_t hl[RPT + 2], hr[RPT + 2];      // raw halo words of segment-end lanes
-    uint32_t prevw[RPT + 2], nextw[RPT + 2];
+    Row<VW> up = load_row<VW, CHECK>(L, y0 - 1);
+    Row<VW> cur = load_row<VW, CHECK>(L, y0);
+    Row<VW> q[kPrefetch];
+#pragma unroll
+    for (int i = 0; i < kPrefetch; ++i) q[i] = load_row<VW, CHECK>(L, y0 + 1 + i);
+    uint32_t up_p = 0, up_n = 0, cur_p, cur_n;
+    if constexpr (MODE == MODE_END) side_words<VW>(L, up, up_p, up_n);
+    side_words<VW>(L, cur, cur_p, cur_n);
 
-    auto fetch = [&](int r) {
-        const int y = y0 - 1 + r;
-        win[r] = load_row<VW>(g, y, c0);
-        hl[r] = seg_first ? load_word(g, y, c0 - 1) : 0u;
-        hr[r] = seg_last ? load_word(g, y, c0 + VW) : 0u;
-    };
-    // words just left and right of this lane's columns in window row r
-    auto neighbours = [&](int r) {
-        uint32_t a = __shfl_up_sync(0xFFFFFFFFu, win[r].v[VW - 1], 1, nvp);
-        uint32_t b = __shfl_down_sync(0xFFFFFFFFu, win[r].v[0], 1, nvp);
-        prevw[r] = seg_first ? hl[r] : a;
-        nextw[r] = seg_last ? hr[r] : b;
-    };
-
+#pragma unroll 1
+    for (int r0 = 0; r0 < RPT; r0 += kPrefetch) {
 #pragma unroll
-    for (int r = 0; r <= kPrefetch && r < RPT + 2; ++r) fetch(r);
-    if constexpr (MODE == MODE_END) neighbours(0);
-
-#pragma unroll
-    for (int r = 1; r <= RPT; ++r) {
-        if (r + kPrefetch < RPT + 2) fetch(r + kPrefetch);
-        if constexpr (MODE == MODE_END) {
-            if (r == 1) neighbours(1);
-            neighbours(r + 1);
-        } else {
-            neighbours(r);
-        }
-        const int y = y0 - 1 + r;
-        Words<VW> e0, e1, e2, e3;
-#pragma unroll
-        for (int k = 0; k < VW; ++k) {
-            const uint32_t cur = win[r].v[k];
-            const uint32_t pv = (k == 0) ? prevw[r] : win[r].v[k - 1];
-            const uint32_t nx = (k == VW - 1) ? nextw[r] : win[r].v[k + 1];
-            const uint32_t L = from_left(pv, cur);      // I(x-1, y)
-            const uint32_t R = from_right(cur, nx);     // I(x+1, y)
-            const uint32_t U = win[r - 1].v[k];         // I(x, y-1)
-            const uint32_t D = win[r + 1].v[k];         // I(x, y+1)
-            const uint32_t M = ~cur;                    // the mask
-            const uint32_t valid = (c0 + k == g.nw - 1) ? g.lastmask : kAllOnes;
-            if constexpr (MODE == MODE_EDGE) {
-                e0.v[k] = M & (L | R | U | D) & valid;
-            } else if constexpr (MODE == MODE_DISPLAY) {
-                e0.v[k] = ~(M & (L | R | U | D)) & valid;
-            } else if constexpr (MODE == MODE_FUND) {
-                e0.v[k] = M & L & valid;
-                e1.v[k] = M & R & valid;
-                e2.v[k] = M & U & valid;
-                e3.v[k] = M & D & valid;
-            } else {
-                // Fig. 1 neighbours 1..8 of every pixel of the word, as
-                // "is white" planes; count the black ones bit-sliced and
-                // keep pixels with at most one.
-                const uint32_t pu = (k == 0) ? prevw[r - 1] : win[r - 1].v[k - 1];
-                const uint32_t nu = (k == VW - 1) ? nextw[r - 1] : win[r - 1].v[k + 1];
-                const uint32_t pd = (k == 0) ? prevw[r + 1] : win[r + 1].v[k - 1];
-                const uint32_t nd = (k == VW - 1) ? nextw[r + 1] : win[r + 1].v[k + 1];
-                const uint32_t nb[8] = {
-                    from_right(U, nu),   // 1: up-right
-                    U,                   // 2: up
-                    from_left(pu, U),    // 3: up-left
-                    L,                   // 4: left
-                    from_left(pd, D),    // 5: down-left
-                    D,                   // 6: down
-                    from_right(D, nd),   // 7: down-right
-                    R                    // 8: right
-                };
-                uint32_t one = 0, two = 0;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint32_t black = ~nb[j];
-                    two |= one & black;
-                    one |= black;
-                }
-                e0.v[k] = M & ~two & valid;
-            }
-        }
-        store_row<VW>(g, o.p[0], y, c0, e0);
-        if constexpr (MODE == MODE_FUND) {
-            store_row<VW>(g, o.p[1], y, c0, e1);
-            store_row<VW>(g, o.p[2], y, c0, e2);
-            store_row<VW>(g, o.p[3], y, c0, e3);
+        for (int j = 0; j < kPrefetch; ++j) {
+            const int y = y0 + r0 + j;
+            const Row<VW> dn = q[j];
+            if (r0 + j + 1 + kPrefetch <= RPT) q[j] = load_row<VW, CHECK>(L, y + 1 + kPrefetch);
+            uint32_t dn_p, dn_n;
+            side_words<VW>(L, dn, dn_p, dn_n);
+            if (L.active && rows_left && (!CHECK || y < g.h))
+                emit_row<VW, MODE>(L, y, up, cur, dn, cur_p, cur_n, up_p, up_n, dn_p, dn_n);
+            up = cur;
+            cur = dn;
+            up_p = cur_p;
+            up_n = cur_n;
+            cur_p = dn_p;
+            cur_n = dn_n;
         }
     }
+}
+
+template <int VW, int RPT, int MODE>
+__device__ __forceinline__ void window_tile(const Geo &g, const Outs &o, int cb, int rb,
+                                            int lane) {
+    const int rows_per_task = RPT << (5 - g.seg_log2);
+    const int top = rb * rows_per_task;
+    if (top >= 1 && top + rows_per_task < g.h)
+        window_tile_rows<VW, RPT, MODE, false>(g, o, cb, rb, lane);
+    else
+        window_tile_rows<VW, RPT, MODE, true>(g, o, cb, rb, lane);
 }
 
 }  // namespace me

@@ -76,8 +76,12 @@ def test_argument_errors_without_a_gpu(lib):
     assert L.me_edges_batch(None, 0, None) == lib.C["ME_OK"]
     bad = lib.make_descs([(a, a, 8, 8, 1, 0)])
     assert L.me_edges_batch(bad, 1, None) == ALIAS
-    cfg = lib.me_tile_cfg(0, 3, 4, 256, 0)
+    cfg = lib.me_tile_cfg(0, 3, 4, 256, 0, 32, 4)
     assert L.me_set_tile_cfg(0, ctypes.byref(cfg)) == ARG      # rows_per_lane 3
+    cfg = lib.me_tile_cfg(1, 8, 4, 256, 0, 64, 4)
+    assert L.me_set_tile_cfg(0, ctypes.byref(cfg)) == ARG      # 256 KiB of stages
+    cfg = lib.me_tile_cfg(1, 8, 4, 256, 0, 32, 1)
+    assert L.me_set_tile_cfg(1, ctypes.byref(cfg)) == ARG      # one stage
     assert L.me_set_tile_cfg(7, ctypes.byref(cfg)) == ARG
     assert L.me_serve_open(None, None) == ARG
     assert L.me_serve_poll(None, 1, None, 0, None) == ARG
@@ -88,7 +92,7 @@ def test_tile_cfg_roundtrip(lib):
     L = lib.load()
     old = lib.me_tile_cfg()
     assert L.me_get_tile_cfg(1, ctypes.byref(old)) == 0
-    new = lib.me_tile_cfg(0, 16, 4, 512, 2)
+    new = lib.me_tile_cfg(1, 16, 4, 512, 2, 48, 3)
     assert L.me_set_tile_cfg(1, ctypes.byref(new)) == 0
     assert lib.me_get_tile_cfg(1).as_dict() == new.as_dict()
     assert L.me_set_tile_cfg(1, ctypes.byref(old)) == 0

@@ -87,20 +87,38 @@ def test_repeated_calls_reuse_graphs_and_slots():
             check_batch(imgs, srcs, dsts)
 
 
+def batch_cfgs():
+    out = []
+    for rows, threads, ctas, vec in itertools.product([4, 8, 16, 32], [128, 256, 512],
+                                                      [1, 2, 8], [1, 4]):
+        out.append((0, rows, vec, threads, ctas, 32, 4))
+    for kb, st, threads, ctas in itertools.product([4, 16, 32, 64], [2, 3, 4],
+                                                   [128, 256, 512], [0, 1, 2]):
+        if kb * st <= 216:
+            out.append((1, 8, 4, threads, ctas, kb, st))
+    return out
+
+
 def test_every_batch_configuration():
     L = _lib.load()
     saved = _lib.me_get_tile_cfg(1)
-    imgs, srcs, dsts, items = make_batch(3, 50, 1, 1200)
+    imgs, srcs, dsts, items = make_batch(3, 50, 1, 1200, offs=[0, 0, 0, 1])
+    # one very wide image forces column strips in the bulk engine
+    wide = (np.random.default_rng(9).random((21, 30000)) < 0.5).astype(np.uint8)
+    words = S.pack(wide, S.batch_stride(30000), pad="random", seed=3)
+    src, dst = DevBuf(words), DevBuf(np.zeros_like(words), fill=SENTINEL)
+    imgs.append((wide, 0)); srcs.append(src); dsts.append(dst)
+    items.append((src.ptr(), dst.ptr(), 30000, 21, words.shape[1], 0))
     descs = _lib.make_descs(items)
     try:
-        for rows, threads, ctas, vec in itertools.product([4, 8, 16, 32], [128, 256, 512],
-                                                          [1, 2, 8], [1, 4]):
-            assert _lib.me_set_tile_cfg(1, _lib.me_tile_cfg(0, rows, vec, threads, ctas)) == 0
+        for c in batch_cfgs():
+            assert _lib.me_set_tile_cfg(1, _lib.me_tile_cfg(*c)) == 0, c
             for d in dsts:
                 d.t.fill_(int(np.uint32(SENTINEL).view(np.int32)))
             assert _lib.me_edges_batch(descs, len(items)) == 0
             sync()
             check_batch(imgs, srcs, dsts)
+        assert _lib.me_device_faults(clear=True) == 0
     finally:
         L.me_set_tile_cfg(1, saved)
 

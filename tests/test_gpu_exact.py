@@ -161,23 +161,55 @@ def all_single_cfgs():
     out = []
     for rows, threads, ctas, vec in itertools.product([4, 8, 16, 32], [128, 256, 512],
                                                       [0, 1, 3], [1, 4]):
-        out.append((0, rows, vec, threads, ctas))
+        out.append((0, rows, vec, threads, ctas, 32, 4))
+    for kb, st, threads, ctas in itertools.product([4, 8, 16, 32, 64], [2, 3, 4],
+                                                   [128, 256, 512], [0, 1]):
+        if kb * st <= 216:
+            out.append((1, 8, 4, threads, ctas, kb, st))
     return out
 
 
 def test_every_tile_configuration():
+    """Every engine and tile shape on ragged images: whole-row bands,
+    column strips (rows wider than a stage), unaligned rows (cooperative
+    loads, 32-bit stores) and tiny images."""
     L = _lib.load()
     saved = _lib.me_get_tile_cfg(0)
-    cases = [(rand_img(s, h, w, 0.5), w, h) for s, (w, h) in
-             enumerate([(97, 45), (4100, 37), (300, 129), (33, 1000), (1, 70)])]
-    refs = [O.edges(img, 0) for img, _, _ in cases]
+    shapes = [(97, 45), (4100, 37), (300, 129), (33, 1000), (1, 70), (40000, 19)]
+    cases = []
+    for s_, (w, h) in enumerate(shapes):
+        img = rand_img(s_, h, w, 0.5)
+        ref = O.edges(img, 0)
+        cases.append((img, ref, S.round_up(S.words_per_row(w), 4), 0))
+        cases.append((img, ref, S.words_per_row(w) + 1, 1))
     try:
         for c in all_single_cfgs():
-            cfg = _lib.me_tile_cfg(*c)
-            assert _lib.me_set_tile_cfg(0, cfg) == 0, c
-            for (img, w, h), ref in zip(cases, refs):
-                got = run_single(edges_fused, img, stride=S.round_up(S.words_per_row(w), 4))
-                assert np.array_equal(got, ref), (c, w, h)
+            assert _lib.me_set_tile_cfg(0, _lib.me_tile_cfg(*c)) == 0, c
+            for img, ref, stride, off in cases:
+                got = run_single(edges_fused, img, stride=stride, off=off)
+                assert np.array_equal(got, ref), (c, img.shape, stride, off)
+        assert _lib.me_device_faults(clear=True) == 0
+    finally:
+        L.me_set_tile_cfg(0, saved)
+
+
+@pytest.mark.parametrize("kb,stages", [(32, 4), (64, 3), (8, 2)])
+def test_bulk_engine_32768(kb, stages):
+    """The bulk engine on the 1-Gpixel image, compared in full."""
+    import torch
+    L = _lib.load()
+    saved = _lib.me_get_tile_cfg(0)
+    w = h = 32768
+    words = S.blocks_packed(w, h, seed=1)
+    want = O.edges(S.unpack(words, w), 0)
+    x = torch.from_numpy(words.view(np.int32)).cuda()
+    y = torch.empty_like(x)
+    try:
+        assert _lib.me_set_tile_cfg(0, _lib.me_tile_cfg(1, 8, 4, 512, 0, kb, stages)) == 0
+        assert _lib.me_edges(x, w, h, words.shape[1], y, 0) == 0
+        sync()
+        assert np.array_equal(S.unpack(y.cpu().numpy().view(np.uint32), w), want)
+        assert _lib.me_device_faults(clear=True) == 0
     finally:
         L.me_set_tile_cfg(0, saved)
 
