@@ -20,8 +20,9 @@
  * 2: one bit per pixel, 0 for black, 1 for white).  nw = ceil(w / 32) words
  * of a row hold pixels; bits x >= w of word nw-1 and words nw .. stride-1
  * are padding.  Input padding is ignored (read as outside the image).  In
- * every output, the padding bits of word nw-1 are written 0 and words
- * nw .. stride-1 are left untouched.
+ * every output, the padding bits of word nw-1 and the padding words
+ * nw .. stride-1 are written 0, so whole rows are written (no output sector
+ * is ever partly written and read back).
  *
  * Edge polarity: an output bit of 1 marks an edge point (Edge(p) = logic 1,
  * Section 1).  Section 5 inverts the OR only to draw edges black on white;
@@ -300,8 +301,8 @@ int me_serve_submit(me_server *srv, const uint32_t *host_img, int32_t w,
 /*
  * Collect a result.  Waits up to timeout_us microseconds (0: do not wait,
  * negative: wait without limit) and returns ME_OK with the edge map copied
- * to host_edge (h rows of the request's stride_words; padding words
- * untouched) and the timing in *t (may be NULL); ME_PENDING (timeout 0) or
+ * to host_edge (h rows of the request's stride_words, padding written 0)
+ * and the timing in *t (may be NULL); ME_PENDING (timeout 0) or
  * ME_TIMEOUT when not ready; ME_ERR_TICKET for an unknown or already
  * collected ticket.  A collected ticket is forgotten.
  */

@@ -93,7 +93,7 @@ Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
     g.lastmask = (w & 31) ? ((1u << (w & 31)) - 1u) : kAllOnes;
     g.fill = (boundary == ME_BOUNDARY_WHITE) ? kAllOnes : 0u;
     g.vw = vw;
-    g.nv = (g.nw + vw - 1) / vw;
+    g.nv = (stride + vw - 1) / vw;      // output covers the whole stride
     g.seg_log2 = g.nv >= 32 ? 5 : ceil_log2(g.nv);
     g.ncb = g.seg_log2 == 5 ? (g.nv + 31) / 32 : 1;
     return g;
@@ -102,8 +102,8 @@ Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
 // ------------------------------------------------------------ tile configs
 static std::mutex g_cfg_mu;
 static me_tile_cfg g_cfg[2] = {
-    {ME_ENGINE_REGS, 8, 4, 256, 0, 32, 4},     // single image
-    {ME_ENGINE_REGS, 8, 4, 256, 4, 32, 4},     // batch
+    {ME_ENGINE_REGS, 4, 4, 128, 0, 32, 4},     // single image
+    {ME_ENGINE_REGS, 4, 4, 256, 8, 32, 4},     // batch
 };
 
 void apply_tune_cache(int kind);
@@ -259,7 +259,7 @@ int me_edges_staged(const uint32_t *img, int32_t w, int32_t h,
     if (rc != ME_OK) return rc;
     if ((rc = check_device_ptr(img)) != ME_OK) return rc;
     if ((rc = check_device_ptr(edge)) != ME_OK) return rc;
-    if ((uint64_t)h * (uint64_t)((w + 31) / 32) >= (1ull << 32)) return ME_ERR_ARG;
+    if ((uint64_t)h * (uint64_t)stride_words >= (1ull << 32)) return ME_ERR_ARG;
     const cudaStream_t s = (cudaStream_t)stream;
     const Geo g = make_geo(img, w, h, stride_words, boundary, 1);
     uint32_t *mask = nullptr;

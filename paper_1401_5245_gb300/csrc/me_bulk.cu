@@ -49,7 +49,7 @@ __device__ __forceinline__ Band band_of(const KDescB &d, int local) {
     b.y0 = rb * d.band_rows;
     b.rows = min(d.band_rows, d.h - b.y0);
     b.x0 = cb * d.band_words;
-    b.words = min(d.band_words, d.nw - b.x0);
+    b.words = min(d.band_words, d.stride - b.x0);     // padding words are written 0
     b.ya = max(0, b.y0 - 1);
     b.yb = min(d.h, b.y0 + d.band_rows + 1);
     if (d.flags & kRowMode) {
@@ -64,10 +64,9 @@ __device__ __forceinline__ Band band_of(const KDescB &d, int local) {
     return b;
 }
 
-__device__ __forceinline__ uint32_t fixw(const KDescB &d, int x, uint32_t v) {
-    if (x >= d.nw) return d.fill;
-    if (x == d.nw - 1) return (v & d.lastmask) | (d.fill & ~d.lastmask);
-    return v;
+// Bits of image word x that hold pixels (0 for words outside the row).
+__device__ __forceinline__ uint32_t col_keep(const KDescB &d, int x) {
+    return x < d.nw - 1 ? kAllOnes : (x == d.nw - 1 ? d.lastmask : 0u);
 }
 
 // Warp 0: start the copies of band `local` of image d into `stage`.
@@ -108,51 +107,94 @@ __device__ __forceinline__ void consume(const KDescB &d, int local, uint32_t *st
         }
         __syncthreads();
     }
-    const int q = (b.words + 3) >> 2;               // 4-word groups per row
-    const int items = b.rows * q;
+    // Lanes form row segments of nvp lanes, one 4-word group each (narrow
+    // bands fold the warp).  A segment walks a run of rows of one column
+    // block, keeping the rows above, at and below the output row in
+    // registers; the words left and right of its group come from shared
+    // memory, so segments never exchange data and may diverge freely.
+    const int ncol4 = (b.words + 3) >> 2;
+    const int seg_log2 = ncol4 >= 32 ? 5 : 32 - __clz(ncol4 - 1);
+    const int nvp = 1 << seg_log2;
+    const int ncb = (ncol4 + nvp - 1) >> seg_log2;
+    const int nseg = (int)(blockDim.x >> 5) << (5 - seg_log2);
+    const int rr = max(4, (b.rows * ncb + nseg - 1) / nseg);
+    const int nruns = (b.rows + rr - 1) / rr;
+    const int units = ncb * nruns;
+    const int lane = threadIdx.x & 31;
+    const int col = lane & (nvp - 1);
+    const int gseg = (int)((threadIdx.x >> 5) << (5 - seg_log2)) + (lane >> seg_log2);
     const bool vec_store = (d.flags & kVecStore) != 0;
-    for (int i = threadIdx.x; i < items; i += blockDim.x) {
-        const int r = i / q;
-        const int x = b.x0 + 4 * (i - r * q);
-        const int y = b.y0 + r;
-        const uint32_t *row = stage + (size_t)(y - b.ya) * d.pitch + (x - b.xb);
-        const uint4 c4 = lds128(row);
-        uint32_t cur[4] = {fixw(d, x, c4.x), fixw(d, x + 1, c4.y), fixw(d, x + 2, c4.z),
-                           fixw(d, x + 3, c4.w)};
-        uint32_t up[4], dn[4];
-        if (y > 0) {
-            const uint4 u = lds128(row - d.pitch);
-            up[0] = fixw(d, x, u.x); up[1] = fixw(d, x + 1, u.y);
-            up[2] = fixw(d, x + 2, u.z); up[3] = fixw(d, x + 3, u.w);
+    for (int u = gseg; u < units; u += nseg) {
+        const int cb = u % ncb, run = u / ncb;
+        const int x = b.x0 + 4 * (cb * 32 + col);
+        if (x >= b.x0 + b.words) continue;
+        const int ys = b.y0 + run * rr;
+        const int ye = min(ys + rr, b.y0 + b.rows);
+        // outside colour per word of the group: fixed = (raw & keep) | fb
+        uint32_t keep[4], fb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            keep[k] = col_keep(d, x + k);
+            fb[k] = d.fill & ~keep[k];
+        }
+        const uint32_t nkeep = col_keep(d, x + 4), nfb = d.fill & ~nkeep;
+        const uint32_t pkeep = x > 0 ? kAllOnes : 0u, pfb = d.fill & ~pkeep;
+        const int cx = x - b.xb;                         // stage column of word x
+        const int cp = max(cx - 1, 0), cn = min(cx + 4, d.pitch - 1);
+        const uint32_t *srow = stage + (size_t)(ys - b.ya) * d.pitch;
+        uint32_t up[4], cur[4], cur_p, cur_n;
+        if (ys > 0) {
+            const uint4 v = lds128(srow - d.pitch + cx);
+            up[0] = (v.x & keep[0]) | fb[0]; up[1] = (v.y & keep[1]) | fb[1];
+            up[2] = (v.z & keep[2]) | fb[2]; up[3] = (v.w & keep[3]) | fb[3];
         } else {
             up[0] = up[1] = up[2] = up[3] = d.fill;
         }
-        if (y + 1 < d.h) {
-            const uint4 v = lds128(row + d.pitch);
-            dn[0] = fixw(d, x, v.x); dn[1] = fixw(d, x + 1, v.y);
-            dn[2] = fixw(d, x + 2, v.z); dn[3] = fixw(d, x + 3, v.w);
-        } else {
-            dn[0] = dn[1] = dn[2] = dn[3] = d.fill;
+        {
+            const uint4 v = lds128(srow + cx);
+            cur[0] = (v.x & keep[0]) | fb[0]; cur[1] = (v.y & keep[1]) | fb[1];
+            cur[2] = (v.z & keep[2]) | fb[2]; cur[3] = (v.w & keep[3]) | fb[3];
+            cur_p = (srow[cp] & pkeep) | pfb;
+            cur_n = (srow[cn] & nkeep) | nfb;
         }
-        const uint32_t prev = (x > 0) ? row[-1] : d.fill;
-        const uint32_t next = (x + 4 < d.nw) ? fixw(d, x + 4, row[4]) : d.fill;
-        uint32_t e[4];
+        uint32_t *orow = d.edge + (size_t)ys * d.stride + x;
+        for (int y = ys; y < ye; ++y) {
+            srow += d.pitch;
+            uint32_t dn[4], dn_p, dn_n;
+            if (y + 1 < d.h) {
+                const uint4 v = lds128(srow + cx);
+                dn[0] = (v.x & keep[0]) | fb[0]; dn[1] = (v.y & keep[1]) | fb[1];
+                dn[2] = (v.z & keep[2]) | fb[2]; dn[3] = (v.w & keep[3]) | fb[3];
+                dn_p = (srow[cp] & pkeep) | pfb;
+                dn_n = (srow[cn] & nkeep) | nfb;
+            } else {
+                dn[0] = dn[1] = dn[2] = dn[3] = dn_p = dn_n = d.fill;
+            }
+            uint32_t e[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t pv = k == 0 ? prev : cur[k - 1];
-            const uint32_t nx = k == 3 ? next : cur[k + 1];
-            const uint32_t L = __funnelshift_l(pv, cur[k], 1);   // I(x-1, y)
-            const uint32_t R = __funnelshift_r(cur[k], nx, 1);   // I(x+1, y)
-            const uint32_t valid = (x + k == d.nw - 1) ? d.lastmask : kAllOnes;
-            e[k] = ~cur[k] & (L | R | up[k] | dn[k]) & valid;
-        }
-        uint32_t *out = d.edge + (size_t)y * d.stride + x;
-        if (vec_store && x + 3 < d.nw) {
-            __stcs(reinterpret_cast<uint4 *>(out), make_uint4(e[0], e[1], e[2], e[3]));
-        } else {
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t pv = k == 0 ? cur_p : cur[k - 1];
+                const uint32_t nx = k == 3 ? cur_n : cur[k + 1];
+                const uint32_t L = __funnelshift_l(pv, cur[k], 1);   // I(x-1, y)
+                const uint32_t R = __funnelshift_r(cur[k], nx, 1);   // I(x+1, y)
+                e[k] = ~cur[k] & (L | R | up[k] | dn[k]) & keep[k];
+            }
+            if (vec_store) {
+                // stride % 4 == 0: the group lies inside the row
+                __stcs(reinterpret_cast<uint4 *>(orow), make_uint4(e[0], e[1], e[2], e[3]));
+            } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (x + k < d.nw) __stcs(out + k, e[k]);
+                for (int k = 0; k < 4; ++k)
+                    if (x + k < d.stride) __stcs(orow + k, e[k]);
+            }
+            orow += d.stride;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                up[k] = cur[k];
+                cur[k] = dn[k];
+            }
+            cur_p = dn_p;
+            cur_n = dn_n;
         }
     }
 }
@@ -266,7 +308,7 @@ void bulk_geometry(const Geo &g, const void *edge, int stage_words, KDescB *d) {
         if (bw < 32) continue;
         const int eff_r = std::min(r, g.h);
         const double c = (double)(std::min(eff_r + 2, g.h) - eff_r) / eff_r +
-                         (double)(2 * kHalo) / std::min(bw, g.nw + 2 * kHalo);
+                         (double)(2 * kHalo) / std::min(bw, g.stride + 2 * kHalo);
         if (c < cost_b) {
             cost_b = c;
             rows_b = r;
@@ -276,14 +318,14 @@ void bulk_geometry(const Geo &g, const void *edge, int stage_words, KDescB *d) {
     if (rows_a > 0 && cost_a <= cost_b) {
         d->flags |= kRowMode;
         d->band_rows = rows_a;
-        d->band_words = g.nw;
+        d->band_words = g.stride;
         d->pitch = aligned ? g.stride : row_words;
         d->ncb = 1;
     } else {
         d->band_rows = rows_b;
         d->band_words = words_b;
         d->pitch = words_b + 2 * kHalo;
-        d->ncb = (g.nw + words_b - 1) / words_b;
+        d->ncb = (g.stride + words_b - 1) / words_b;
     }
     d->nrb = (g.h + d->band_rows - 1) / d->band_rows;
 }

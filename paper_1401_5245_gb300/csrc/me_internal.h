@@ -28,7 +28,7 @@ struct Geo {
     uint32_t lastmask;          // valid bits of word nw - 1
     uint32_t fill;              // outside colour as a word: ~0 white, 0 black
     int32_t vw;                 // words per lane and row: 4 or 1
-    int32_t nv;                 // vector columns: ceil(nw / vw)
+    int32_t nv;                 // vector columns written: ceil(stride / vw)
     int32_t seg_log2;           // log2 of the lanes one row segment uses
     int32_t ncb;                // column blocks of 32 vector columns
 };

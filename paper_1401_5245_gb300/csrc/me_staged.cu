@@ -16,12 +16,14 @@ namespace me {
 struct StageGeo {
     int32_t h, stride, nw;
     uint32_t lastmask, fill;
-    uint32_t words;          // h * nw (< 2^32, checked by the launcher)
+    uint32_t words;          // h * stride (< 2^32, checked by the launcher)
 };
 
+// Word i of the image is word c of row y; every word of every row is
+// visited, padding words included, so outputs are written whole (0 there).
 __device__ __forceinline__ void stage_index(const StageGeo &g, uint32_t i, int &y, int &c) {
-    y = (int)(i / (uint32_t)g.nw);
-    c = (int)(i - (uint32_t)y * (uint32_t)g.nw);
+    y = (int)(i / (uint32_t)g.stride);
+    c = (int)(i - (uint32_t)y * (uint32_t)g.stride);
 }
 
 // Image word with the outside colour in its padding bits.
@@ -39,7 +41,7 @@ __global__ void k_stage_not(const uint32_t *img, uint32_t *M, StageGeo g) {
         int y, c;
         stage_index(g, i, y, c);
         const size_t at = (size_t)y * g.stride + c;
-        const uint32_t valid = (c == g.nw - 1) ? g.lastmask : kAllOnes;
+        const uint32_t valid = c < g.nw - 1 ? kAllOnes : (c == g.nw - 1 ? g.lastmask : 0u);
         M[at] = ~img[at] & valid;
     }
 }
@@ -84,7 +86,7 @@ __global__ void k_stage_vertical(const uint32_t *img, const uint32_t *M, uint32_
 
 cudaError_t launch_staged(const Geo &geo, uint32_t *mask, uint32_t *edge,
                           cudaStream_t s) {
-    const uint64_t words = (uint64_t)geo.h * (uint64_t)geo.nw;
+    const uint64_t words = (uint64_t)geo.h * (uint64_t)geo.stride;
     if (words >= (1ull << 32)) return cudaErrorInvalidValue;
     StageGeo g{geo.h, geo.stride, geo.nw, geo.lastmask, geo.fill, (uint32_t)words};
     DevInfo di;

@@ -63,7 +63,8 @@ struct Lane {
     uint32_t fill;
     uint32_t keep[VW], fb[VW]; // fixed = (raw & keep) | fb
     uint32_t nkeep, nfb;       // the same for the word after the lane
-    bool active;               // c0 < nw
+    bool loads;                // c0 < nw: the lane's words hold pixels
+    bool active;               // c0 < stride: the lane writes output words
     bool seg_first, seg_last, has_prev, has_next;
 };
 
@@ -92,10 +93,11 @@ __device__ __forceinline__ Lane<VW> make_lane(const Geo &g, const Outs &o, int c
     }
     L.nkeep = col_keep<VW>(g, c0 + VW);
     L.nfb = g.fill & ~L.nkeep;
-    L.active = c0 < g.nw;
+    L.loads = c0 < g.nw;
+    L.active = c0 < g.stride;
     L.seg_first = (col == 0);
     L.seg_last = (col == nvp - 1);
-    L.has_prev = L.seg_first && L.active && c0 > 0;
+    L.has_prev = L.seg_first && L.loads && c0 > 0;
     L.has_next = L.seg_last && (c0 + VW < g.nw);
     return L;
 }
@@ -104,7 +106,7 @@ __device__ __forceinline__ Lane<VW> make_lane(const Geo &g, const Outs &o, int c
 template <int VW, bool CHECK>
 __device__ __forceinline__ Row<VW> load_row(const Lane<VW> &L, int y) {
     Row<VW> r;
-    const bool ok = L.active && (!CHECK || (unsigned)y < (unsigned)L.h);
+    const bool ok = L.loads && (!CHECK || (unsigned)y < (unsigned)L.h);
     const uint32_t *p = L.base + (size_t)y * (size_t)L.stride;
     uint32_t raw[VW];
     if constexpr (VW == 4) {
@@ -119,7 +121,7 @@ __device__ __forceinline__ Row<VW> load_row(const Lane<VW> &L, int y) {
 #pragma unroll
     for (int k = 0; k < VW; ++k) {
         const uint32_t f = (raw[k] & L.keep[k]) | L.fb[k];
-        r.w.v[k] = (!CHECK || ok || !L.active) ? f : L.fill;
+        r.w.v[k] = (!CHECK || ok || !L.loads) ? f : L.fill;
     }
     const bool rowok = !CHECK || (unsigned)y < (unsigned)L.h;
     r.hl = (L.has_prev && rowok) ? __ldg(p - 1) : L.fill;
@@ -140,15 +142,12 @@ __device__ __forceinline__ void side_words(const Lane<VW> &L, const Row<VW> &r, 
 template <int VW>
 __device__ __forceinline__ void store_words(const Lane<VW> &L, uint32_t *out, int y,
                                             const uint32_t (&e)[VW]) {
+    // Padding words (nw .. stride-1) are written too, as 0, so every 32-byte
+    // sector of an output row is written whole and never read back.
     uint32_t *p = out + (size_t)y * (size_t)L.stride;
     if constexpr (VW == 4) {
-        if (L.c0 + 3 < L.nw) {
-            __stcs(reinterpret_cast<uint4 *>(p), make_uint4(e[0], e[1], e[2], e[3]));
-            return;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (L.c0 + k < L.nw) __stcs(p + k, e[k]);
+        // stride % 4 == 0 on this path: the group lies inside the row
+        __stcs(reinterpret_cast<uint4 *>(p), make_uint4(e[0], e[1], e[2], e[3]));
     } else {
         __stcs(p, e[0]);
     }

@@ -6,8 +6,8 @@ polarity and the end-point map, on every width 1..97 and 4095..4097,
 strides wider than the row, garbage in padding bits and words, misaligned
 buffers, both boundary colours, the 256x256 glyph images, the 4096x4096
 images of several densities and the 32768x32768 image in the launch
-configuration the benchmark times.  Outputs are checked for untouched
-padding words and intact guard canaries around every buffer.
+configuration the benchmark times.  Outputs are checked for zeroed
+padding bits and words and intact guard canaries around every buffer.
 """
 import itertools
 
