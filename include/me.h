@@ -310,6 +310,15 @@ int me_serve_poll(me_server *srv, uint64_t ticket, uint32_t *host_edge,
                   int64_t timeout_us, me_timing *t);
 
 /*
+ * Forget a ticket.  A request still queued is dropped at once; one already
+ * on the GPU finishes there and its memory is reclaimed when its batch
+ * retires; a finished one is freed.  ME_ERR_TICKET for an unknown ticket.
+ * Polling and cancelling the same ticket from two threads at once is not
+ * allowed.
+ */
+int me_serve_cancel(me_server *srv, uint64_t ticket);
+
+/*
  * Counters since open: requests submitted, completed, batches launched,
  * and the most device bytes ever in use.  Any pointer may be NULL.
  */

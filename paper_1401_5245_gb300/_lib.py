@@ -99,6 +99,7 @@ PROTOTYPES = {
     "me_serve_submit": (ctypes.c_int, [c_vp, c_vp, c_i32, c_i32, c_i32, c_i32,
                                        ctypes.POINTER(c_u64)]),
     "me_serve_poll": (ctypes.c_int, [c_vp, c_u64, c_vp, c_i64, ctypes.POINTER(me_timing)]),
+    "me_serve_cancel": (ctypes.c_int, [c_vp, c_u64]),
     "me_serve_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                                       ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     "me_serve_close": (ctypes.c_int, [c_vp, c_i64]),
@@ -284,6 +285,9 @@ class Server:
         p = host_edge.ctypes.data if hasattr(host_edge, "ctypes") else int(host_edge)
         rc = load().me_serve_poll(self._h, ticket, p, timeout_us, ctypes.byref(tm))
         return rc, tm
+
+    def cancel(self, ticket) -> int:
+        return load().me_serve_cancel(self._h, ticket)
 
     def stats(self):
         v = [c_i64() for _ in range(4)]

@@ -1,15 +1,16 @@
 // me_edges_batch and batch plans: many images in one persistent launch,
 // replayed from CUDA graphs.
 //
-// A call plans the batch on the host (descriptors, each work owner's first
+// A launch plans the batch on the host (descriptors, each work owner's first
 // image), writes the plan into a pinned staging slot and launches that
 // slot's graph: one memcpy node (staging -> device arena) and one kernel
 // node (the persistent batch kernel of the configured engine reading the
-// arena).  Slots form a ring of kRing per device; a slot is reused only
-// after the event recorded behind its last launch has completed, so graphs
-// in flight never see their staging or arena overwritten.  Graphs are
-// cached per slot, keyed by the tile configuration and grid; the memcpy
-// node's size is set per launch.
+// arena).  Slots form a ring (BatchRing); a slot is reused only after the
+// event recorded behind its last launch has completed, so graphs in flight
+// never see their staging or arena overwritten.  Graphs are cached per
+// slot, keyed by the tile configuration and grid; the memcpy node's size is
+// set per launch.  me_edges_batch uses one ring per device; a server owns
+// its own ring.
 #include <algorithm>
 #include <cstring>
 #include <memory>
@@ -31,49 +32,6 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t copy = nullptr;
 };
-
-struct Slot {
-    size_t cap = 0;
-    void *host = nullptr;
-    void *dev = nullptr;
-    cudaEvent_t done = nullptr;
-    bool pending = false;
-    std::unordered_map<uint64_t, GraphEntry> graphs;
-
-    void drop_graphs() {
-        for (auto &kv : graphs) {
-            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
-        }
-        graphs.clear();
-    }
-    void release() {
-        if (pending && done) cudaEventSynchronize(done);
-        pending = false;
-        drop_graphs();
-        if (host) cudaFreeHost(host);
-        if (dev) cudaFree(dev);
-        if (done) cudaEventDestroy(done);
-        host = dev = nullptr;
-        done = nullptr;
-        cap = 0;
-    }
-};
-
-struct DevBatch {
-    std::mutex mu;
-    Slot slots[kRing];
-    int next = 0;
-};
-
-std::mutex g_devs_mu;
-DevBatch *g_devs[64] = {};
-
-DevBatch *dev_state(int dev) {
-    std::lock_guard<std::mutex> lk(g_devs_mu);
-    if (!g_devs[dev]) g_devs[dev] = new DevBatch();
-    return g_devs[dev];
-}
 
 size_t round_pow2(size_t v) {
     size_t c = kMinSlot;
@@ -175,19 +133,124 @@ cudaError_t build_graph(const void *host, void *dev, size_t bytes, const Setup &
 
 }  // namespace
 
+// ------------------------------------------------------------------ ring
+struct BatchRing::Slot {
+    size_t cap = 0;
+    void *host = nullptr;
+    void *dev = nullptr;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+    std::unordered_map<uint64_t, GraphEntry> graphs;
+
+    void drop_graphs() {
+        for (auto &kv : graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+        }
+        graphs.clear();
+    }
+    void release() {
+        if (pending && done) cudaEventSynchronize(done);
+        pending = false;
+        drop_graphs();
+        if (host) cudaFreeHost(host);
+        if (dev) cudaFree(dev);
+        if (done) cudaEventDestroy(done);
+        host = dev = nullptr;
+        done = nullptr;
+        cap = 0;
+    }
+    int reserve(size_t need) {
+        if (cap >= need) return ME_OK;
+        release();
+        const size_t c = round_pow2(need);
+        cudaError_t e;
+        if ((e = cudaHostAlloc(&host, c, cudaHostAllocDefault)) != cudaSuccess) {
+            host = nullptr;
+            return fail(e);
+        }
+        if ((e = cudaMalloc(&dev, c)) != cudaSuccess) {
+            dev = nullptr;
+            release();
+            return fail(e);
+        }
+        if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess) {
+            done = nullptr;
+            release();
+            return fail(e);
+        }
+        cap = c;
+        return ME_OK;
+    }
+};
+
+BatchRing::BatchRing(int nslots) : n_(std::max(1, nslots)), slots_(new Slot[std::max(1, nslots)]) {}
+
+BatchRing::~BatchRing() {
+    release();
+    delete[] slots_;
+}
+
+void BatchRing::release() {
+    std::lock_guard<std::mutex> lk(mu_);
+    for (int i = 0; i < n_; ++i) slots_[i].release();
+}
+
+int BatchRing::launch(const me_desc *descs, int n, cudaStream_t stream) {
+    if (n < 0 || (n > 0 && descs == nullptr)) return ME_ERR_ARG;
+    if (n == 0) return ME_OK;
+    Setup su;
+    int rc = setup_batch(descs, n, tile_cfg(ME_KIND_BATCH), &su);
+    if (rc != ME_OK) return rc;
+    std::lock_guard<std::mutex> lk(mu_);
+    Slot &slot = slots_[next_];
+    next_ = (next_ + 1) % n_;
+    cudaError_t e;
+    if (slot.pending) {
+        if ((e = cudaEventSynchronize(slot.done)) != cudaSuccess) return fail(e);
+        slot.pending = false;
+    }
+    if ((rc = slot.reserve(su.arena)) != ME_OK) return rc;
+    if ((rc = fill_arena(descs, n, su, slot.host)) != ME_OK) return rc;
+    const uint64_t key = cfg_key(su.cfg) * 31 + (uint64_t)su.grid;
+    auto it = slot.graphs.find(key);
+    if (it == slot.graphs.end()) {
+        GraphEntry ge;
+        if ((e = build_graph(slot.host, slot.dev, slot.cap, su, &ge)) != cudaSuccess)
+            return fail(e);
+        it = slot.graphs.emplace(key, ge).first;
+    }
+    // copy only what this batch filled
+    e = cudaGraphExecMemcpyNodeSetParams1D(it->second.exec, it->second.copy, slot.dev,
+                                           slot.host, su.arena, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(e);
+    if ((e = cudaGraphLaunch(it->second.exec, stream)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventRecord(slot.done, stream)) != cudaSuccess) return fail(e);
+    slot.pending = true;
+    return ME_OK;
+}
+
+// ------------------------------------------------------- per-device rings
+namespace {
+std::mutex g_rings_mu;
+BatchRing *g_rings[64] = {};
+
+BatchRing *device_ring(int dev) {
+    std::lock_guard<std::mutex> lk(g_rings_mu);
+    if (!g_rings[dev]) g_rings[dev] = new BatchRing(kRing);
+    return g_rings[dev];
+}
+}  // namespace
+
 int batch_shutdown_all() {
     int cur = 0;
     cudaGetDevice(&cur);
-    std::lock_guard<std::mutex> lk(g_devs_mu);
+    std::lock_guard<std::mutex> lk(g_rings_mu);
     for (int d = 0; d < 64; ++d) {
-        if (!g_devs[d]) continue;
+        if (!g_rings[d]) continue;
         cudaSetDevice(d);
-        {
-            std::lock_guard<std::mutex> lk2(g_devs[d]->mu);
-            for (auto &s : g_devs[d]->slots) s.release();
-        }
-        delete g_devs[d];
-        g_devs[d] = nullptr;
+        delete g_rings[d];
+        g_rings[d] = nullptr;
     }
     cudaSetDevice(cur);
     return ME_OK;
@@ -211,60 +274,15 @@ extern "C" {
 int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream) {
     if (n < 0 || (n > 0 && descs == nullptr)) return ME_ERR_ARG;
     if (n == 0) return ME_OK;
-    Setup su;
-    int rc = setup_batch(descs, n, tile_cfg(ME_KIND_BATCH), &su);
-    if (rc != ME_OK) return rc;
-
     int dev = 0;
+    // descriptors are checked before any CUDA call
+    int64_t units = 0;
+    int rc = batch_tasks(descs, n, tile_cfg(ME_KIND_BATCH), &units);
+    if (rc != ME_OK) return rc;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(e);
-    DevBatch *st = dev_state(dev);
-    std::lock_guard<std::mutex> lk(st->mu);
-    Slot &slot = st->slots[st->next];
-    st->next = (st->next + 1) % kRing;
-    if (slot.pending) {
-        e = cudaEventSynchronize(slot.done);
-        if (e != cudaSuccess) return fail(e);
-        slot.pending = false;
-    }
-    if (slot.cap < su.arena) {
-        slot.release();
-        const size_t cap = round_pow2(su.arena);
-        if ((e = cudaHostAlloc(&slot.host, cap, cudaHostAllocDefault)) != cudaSuccess) {
-            slot.host = nullptr;
-            return fail(e);
-        }
-        if ((e = cudaMalloc(&slot.dev, cap)) != cudaSuccess) {
-            slot.dev = nullptr;
-            slot.release();
-            return fail(e);
-        }
-        if ((e = cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming)) != cudaSuccess) {
-            slot.done = nullptr;
-            slot.release();
-            return fail(e);
-        }
-        slot.cap = cap;
-    }
-    if ((rc = fill_arena(descs, n, su, slot.host)) != ME_OK) return rc;
-
-    const uint64_t key = cfg_key(su.cfg) * 31 + (uint64_t)su.grid;
-    auto it = slot.graphs.find(key);
-    if (it == slot.graphs.end()) {
-        GraphEntry ge;
-        if ((e = build_graph(slot.host, slot.dev, slot.cap, su, &ge)) != cudaSuccess)
-            return fail(e);
-        it = slot.graphs.emplace(key, ge).first;
-    }
-    // copy only what this batch filled
-    e = cudaGraphExecMemcpyNodeSetParams1D(it->second.exec, it->second.copy, slot.dev,
-                                           slot.host, su.arena, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return fail(e);
-    if ((e = cudaGraphLaunch(it->second.exec, (cudaStream_t)stream)) != cudaSuccess)
-        return fail(e);
-    if ((e = cudaEventRecord(slot.done, (cudaStream_t)stream)) != cudaSuccess) return fail(e);
-    slot.pending = true;
-    return ME_OK;
+    if (dev < 0 || dev >= 64) return ME_ERR_UNSUPPORTED;
+    return device_ring(dev)->launch(descs, n, (cudaStream_t)stream);
 }
 
 int me_batch_plan_create(const me_desc *descs, int32_t n, me_stream_t stream,

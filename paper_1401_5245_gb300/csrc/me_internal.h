@@ -4,6 +4,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "me.h"
@@ -148,6 +150,26 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
                int total_warps, void *host_arena, int *bad);
 int batch_tasks(const me_desc *descs, int n, const me_tile_cfg &cfg,
                 int64_t *total_tasks);
+
+// A ring of batch launch slots (pinned staging, device arena, cached
+// graphs).  launch() is thread-safe; a slot is reused only after its last
+// launch completed (waits for it if needed).
+class BatchRing {
+   public:
+    explicit BatchRing(int nslots);
+    ~BatchRing();
+    BatchRing(const BatchRing &) = delete;
+    BatchRing &operator=(const BatchRing &) = delete;
+    int launch(const me_desc *descs, int n, cudaStream_t stream);
+    void release();
+
+   private:
+    struct Slot;
+    int n_;
+    int next_ = 0;
+    Slot *slots_;
+    std::mutex mu_;
+};
 
 // The five staged passes.
 cudaError_t launch_staged(const Geo &g, uint32_t *mask, uint32_t *edge,

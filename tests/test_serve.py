@@ -1,0 +1,181 @@
+"""The serving engine: every served edge map equals the one computed alone,
+under concurrent submitters, a budget small enough to force queuing, heap
+fallback when staging is full, cancellation, timeouts and budget refusal.
+All failures are made on the host (no GPU fault is ever provoked)."""
+import threading
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1401_5245_gb300 import _lib, synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.init()
+    _lib.load()
+
+
+@pytest.fixture(scope="module")
+def pool():
+    """A few images of each serving size class (48x48 glyphs, 1024x1024
+    crops, 2480x3508 pages), plus odd shapes and black boundaries."""
+    p = S.serve_pool(0, per_class=(8, 3, 2))
+    items = [im for cls in p for im in cls]
+    g = np.random.default_rng(1)
+    for w, h in [(1, 1), (33, 7), (100, 1), (5000, 3)]:
+        img = (g.random((h, w)) < 0.5).astype(np.uint8)
+        items.append(S.Image(S.pack(img, S.words_per_row(w) + 1, pad="random"), w, h, 1))
+    return items
+
+
+def alone(im):
+    """The same image through me_edges on the device, alone."""
+    import torch
+    x = torch.from_numpy(im.words.view(np.int32)).cuda()
+    y = torch.zeros_like(x)
+    assert _lib.me_edges(x, im.w, im.h, im.stride_words, y, im.boundary) == 0
+    torch.cuda.synchronize()
+    return y.cpu().numpy().view(np.uint32)
+
+
+def serve_all(srv, ims, threads=1):
+    out = [None] * len(ims)
+    errs = []
+
+    def worker(idx):
+        try:
+            tickets = []
+            for i in idx:
+                im = ims[i]
+                rc, t = srv.submit(np.ascontiguousarray(im.words), im.w, im.h,
+                                   im.stride_words, im.boundary)
+                assert rc == 0, _lib.status_string(rc)
+                tickets.append((i, t))
+            for i, t in tickets:
+                res = np.empty_like(ims[i].words)
+                rc, tm = srv.poll(t, res, -1)
+                assert rc == 0, _lib.status_string(rc)
+                assert tm.total_us >= tm.device_us >= 0 and tm.queue_us >= 0
+                out[i] = res
+        except Exception as e:   # noqa: BLE001
+            errs.append(e)
+
+    ths = [threading.Thread(target=worker, args=(list(range(k, len(ims), threads)),))
+           for k in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert not errs, errs
+    return out
+
+
+def test_served_equals_alone_with_concurrent_submitters(pool):
+    ims = [pool[i % len(pool)] for i in range(120)]
+    refs = {id(im): alone(im) for im in pool}
+    srv = _lib.Server(hbm_budget_bytes=256 << 20, staging_bytes=256 << 20,
+                      max_inflight=3, max_batch=16, tick_us=20)
+    try:
+        out = serve_all(srv, ims, threads=4)
+        for im, res in zip(ims, out):
+            assert np.array_equal(res, refs[id(im)])
+        st = srv.stats()
+        assert st["submitted"] == st["completed"] == len(ims)
+        assert st["batches"] >= 1 and 0 < st["peak_bytes"] <= 256 << 20
+    finally:
+        assert srv.close() == 0
+    # and the alone result is the oracle's
+    for im in pool[:10]:
+        want = O.edges(S.unpack(im.words, im.w), im.boundary)
+        assert np.array_equal(S.unpack(refs[id(im)], im.w), want)
+
+
+def test_small_budget_forces_queueing(pool):
+    """Room for little more than one page at a time: requests wait for
+    memory, are admitted as batches retire, and every result is exact."""
+    page = max(pool, key=lambda im: im.packed_bytes)
+    budget = 2 * page.packed_bytes + (1 << 16)
+    ims = [pool[i % len(pool)] for i in range(60)]
+    refs = {id(im): alone(im) for im in pool}
+    srv = _lib.Server(hbm_budget_bytes=budget, staging_bytes=64 << 20, max_inflight=2,
+                      max_batch=4, tick_us=10)
+    try:
+        out = serve_all(srv, ims, threads=2)
+        for im, res in zip(ims, out):
+            assert np.array_equal(res, refs[id(im)])
+        st = srv.stats()
+        assert st["peak_bytes"] <= budget
+        assert st["batches"] >= len(ims) // 4
+    finally:
+        srv.close()
+
+
+def test_budget_refusal(pool):
+    page = max(pool, key=lambda im: im.packed_bytes)
+    srv = _lib.Server(hbm_budget_bytes=page.packed_bytes, staging_bytes=8 << 20)
+    try:
+        rc, _ = srv.submit(page.words, page.w, page.h, page.stride_words)
+        assert rc == _lib.C["ME_ERR_BUDGET"]
+        small = pool[0]
+        rc, t = srv.submit(small.words, small.w, small.h, small.stride_words)
+        assert rc == 0
+        res = np.empty_like(small.words)
+        assert srv.poll(t, res, -1)[0] == 0
+        assert np.array_equal(res, alone(small))
+    finally:
+        srv.close()
+
+
+def test_staging_full_timeout_cancel_and_unknown_ticket(pool):
+    """Staging for one request only: the second waits in heap memory until
+    the first is collected, so its poll times out deterministically; a
+    cancelled request is forgotten; unknown tickets are refused."""
+    a = pool[-5]                         # a 1024 x 1024 crop or a page
+    span = (a.packed_bytes + 255) // 256 * 256
+    srv = _lib.Server(hbm_budget_bytes=64 << 20, staging_bytes=2 * span,
+                      max_inflight=1, max_batch=1)
+    try:
+        rc, ta = srv.submit(a.words, a.w, a.h, a.stride_words)
+        assert rc == 0
+        rc, tb = srv.submit(a.words, a.w, a.h, a.stride_words)
+        assert rc == 0
+        rc, tc = srv.submit(a.words, a.w, a.h, a.stride_words)
+        assert rc == 0
+        res = np.empty_like(a.words)
+        rc, _ = srv.poll(tb, res, 2000)
+        assert rc in (_lib.C["ME_TIMEOUT"], _lib.C["ME_PENDING"])
+        assert srv.poll(tb, res, 0)[0] == _lib.C["ME_PENDING"]
+        assert srv.cancel(tc) == 0
+        assert srv.poll(tc, res, 0)[0] == _lib.C["ME_ERR_TICKET"]
+        assert srv.poll(ta, res, -1)[0] == 0
+        ref = alone(a)
+        assert np.array_equal(res, ref)
+        res2 = np.empty_like(a.words)
+        assert srv.poll(tb, res2, -1)[0] == 0
+        assert np.array_equal(res2, ref)
+        assert srv.poll(ta, res, 0)[0] == _lib.C["ME_ERR_TICKET"]     # collected
+        assert srv.poll(123456789, res, 0)[0] == _lib.C["ME_ERR_TICKET"]
+        assert srv.cancel(987654321) == _lib.C["ME_ERR_TICKET"]
+    finally:
+        srv.close()
+
+
+def test_close_drops_uncollected_and_bad_args(pool):
+    srv = _lib.Server(hbm_budget_bytes=64 << 20, staging_bytes=64 << 20)
+    for im in pool[:6]:
+        assert srv.submit(im.words, im.w, im.h, im.stride_words)[0] == 0
+    assert srv.submit(pool[0].words, 0, 5, 1)[0] == _lib.C["ME_ERR_ARG"]
+    assert srv.submit(pool[0].words, 100, 5, 1)[0] == _lib.C["ME_ERR_ARG"]   # stride
+    assert srv.close(-1) == 0
+    L = _lib.load()
+    cfg = _lib.me_serve_cfg(0, 0, 1, 1, 10, 0)
+    h = _lib.c_vp()
+    import ctypes
+    assert L.me_serve_open(ctypes.byref(cfg), ctypes.byref(h)) == _lib.C["ME_ERR_ARG"]
