@@ -24,7 +24,7 @@
  * nw .. stride-1 are written 0, so whole rows are written (no output sector
  * is ever partly written and read back).
  *
- * Edge polarity: an output bit of 1 marks an edge point (Edge(p) = logic 1,
+ * Edge polarity: an output bit of 1 marks an edge point (Edge(p) true,
  * Section 1).  Section 5 inverts the OR only to draw edges black on white;
  * me_edges_display gives that drawn form.
  *
@@ -169,8 +169,8 @@ int me_edges_display(const uint32_t *img, int32_t w, int32_t h,
  * Second clause of the Section 1 definition on its own: out = 1 at a black
  * pixel with at most one black 8-neighbour (Fig. 1 neighbours 1-8), i.e.
  * isolated points and the ends of one-pixel lines.  Every such point is
- * also an edge point of me_edges (Section 1: the other cases are included
- * in the four types).  Arguments as me_edges.
+ * also an edge point of me_edges (Section 1: the two-clause definition
+ * reduces to the four edge-point types).  Arguments as me_edges.
  */
 int me_end_points(const uint32_t *img, int32_t w, int32_t h,
                   int32_t stride_words, uint32_t *out, int32_t boundary,

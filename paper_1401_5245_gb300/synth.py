@@ -5,8 +5,8 @@ bitmap. It holds none of the edge arithmetic (no mask, no shift, no AND/OR of
 neighbours), so both the CUDA path and the CPU oracle can take their inputs
 from it without sharing any of the method.
 
-Pixel convention (Section 2 of the paper: a monochrome bitmap is a bit-stream
-with 0 for a black pixel and 1 for a white one):
+Pixel convention (Section 2 of the paper: a monochrome bitmap holds one bit
+per pixel, 0 for black and 1 for white):
 
 * byte image  ``u8[h, w]``: one byte per pixel, 0 = black, 1 = white.
 * packed rows ``uint32[h, stride_words]``: pixel (x, y) is bit ``x % 32`` of

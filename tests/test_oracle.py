@@ -43,9 +43,9 @@ def all_images(w, h):
 # ---------------------------------------------------------------------------
 
 def test_lemma_every_3x3_neighbourhood():
-    """Section 1 says the other neighbour cases are included in the four
-    types: a black point with <= 1 black 8-neighbour always has a white
-    4-neighbour.  Check it, and the oracle, on all 512 neighbourhoods."""
+    """Section 1 claims the two-clause definition reduces to the four
+    edge-point types: a black point with <= 1 black 8-neighbour always has a
+    white 4-neighbour.  Check it, and the oracle, on all 512 neighbourhoods."""
     extra = 0
     for code in range(512):
         img = np.array([(code >> k) & 1 for k in range(9)],
