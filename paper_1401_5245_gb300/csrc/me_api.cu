@@ -95,7 +95,7 @@ Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
     g.vw = vw;
     g.nv = (stride + vw - 1) / vw;      // output covers the whole stride
     g.seg_log2 = g.nv >= 32 ? 5 : ceil_log2(g.nv);
-    g.ncb = g.seg_log2 == 5 ? (g.nv + 31) / 32 : 1;
+    g.ncb = g.nv > 32 ? (g.nv + kWideLanes - 1) / kWideLanes : 1;
     return g;
 }
 

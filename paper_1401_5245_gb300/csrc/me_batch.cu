@@ -70,7 +70,7 @@ int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, Setup *s) {
         if (occ < 1) return ME_ERR_ARG;
         const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
         s->grid = di.sm_count * per_sm;
-        s->threads = cfg.cta_threads;
+        s->threads = bulk_threads(cfg);
         s->smem = bulk_smem_bytes(cfg);
         s->stage_words = (int)(s->smem / cfg.stages / 4);
         s->arena = bulk_arena_bytes(n, s->grid);

@@ -3,13 +3,14 @@
 // Persistent CTAs; CTA g owns a contiguous run of bands (row bands of one
 // image, top to bottom, column strip after column strip), so the halo rows
 // a band re-reads were copied moments before for the previous band and come
-// from L2.  Warp 0 produces: for the band `stages` ahead it arms the stage's
-// mbarrier with the byte count and issues cp.async.bulk copies (one per band
-// when the band is whole rows -- contiguous in memory -- else one per row).
-// All warps consume: wait on the stage's barrier, compute every output word
-// of the band from shared memory, store it with 128-bit streaming stores,
-// then release the stage to the producer.  Images whose rows are not 16-byte
-// aligned take the same path with plain cooperative loads into the stage.
+// from L2.  One producer warp walks the run ahead of the consumers: as soon
+// as a stage is released it arms the stage's mbarrier with the byte count
+// and issues cp.async.bulk copies (one per band when the band is whole rows
+// -- contiguous in memory -- else one per row).  The consumer warps wait on
+// a stage, compute every output word of its band from shared memory, store
+// them with 128-bit streaming stores and release the stage.  Images whose
+// rows are not 16-byte aligned take the same path with plain cooperative
+// loads into the stage.
 //
 // Per output word (least significant bit = leftmost pixel):
 //   E = ~I & ((I << 1 | prev >> 31) | (I >> 1 | next << 31) | up | down)
@@ -29,6 +30,7 @@ __device__ unsigned int g_me_fault_flags = 0;
 constexpr unsigned int kFaultBulkWait = 1u;
 
 constexpr int kMaxStages = 8;
+constexpr int kMaxBulkThreads = 512 + 32;  // consumers + one producer warp
 constexpr int kHalo = 4;                 // halo words each side in column mode
 
 namespace {
@@ -95,17 +97,24 @@ __device__ __forceinline__ void produce(const KDescB &d, int local, uint32_t *st
     }
 }
 
-// All threads: the band's output words from the stage.
-__device__ __forceinline__ void consume(const KDescB &d, int local, uint32_t *stage) {
+// Barrier among the consumer warps only (the producer warp keeps running).
+__device__ __forceinline__ void consumers_sync(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Consumer threads tid = 0 .. nthreads-1: the band's output words from the
+// stage.
+__device__ __forceinline__ void consume(const KDescB &d, int local, uint32_t *stage, int tid,
+                                        int nthreads) {
     const Band b = band_of(d, local);
     if (!(d.flags & kBulkCopy)) {
         const int nrows = b.yb - b.ya, nwords = b.xe - b.xs;
-        for (int i = threadIdx.x; i < nrows * nwords; i += blockDim.x) {
+        for (int i = tid; i < nrows * nwords; i += nthreads) {
             const int r = i / nwords, c = i - r * nwords;
             stage[r * d.pitch + (b.xs - b.xb) + c] =
                 __ldg(d.img + (size_t)(b.ya + r) * d.stride + b.xs + c);
         }
-        __syncthreads();
+        consumers_sync(nthreads);
     }
     // Lanes form row segments of nvp lanes, one 4-word group each (narrow
     // bands fold the warp).  A segment walks a run of rows of one column
@@ -116,13 +125,13 @@ __device__ __forceinline__ void consume(const KDescB &d, int local, uint32_t *st
     const int seg_log2 = ncol4 >= 32 ? 5 : 32 - __clz(ncol4 - 1);
     const int nvp = 1 << seg_log2;
     const int ncb = (ncol4 + nvp - 1) >> seg_log2;
-    const int nseg = (int)(blockDim.x >> 5) << (5 - seg_log2);
+    const int nseg = (nthreads >> 5) << (5 - seg_log2);
     const int rr = max(4, (b.rows * ncb + nseg - 1) / nseg);
     const int nruns = (b.rows + rr - 1) / rr;
     const int units = ncb * nruns;
-    const int lane = threadIdx.x & 31;
+    const int lane = tid & 31;
     const int col = lane & (nvp - 1);
-    const int gseg = (int)((threadIdx.x >> 5) << (5 - seg_log2)) + (lane >> seg_log2);
+    const int gseg = ((tid >> 5) << (5 - seg_log2)) + (lane >> seg_log2);
     const bool vec_store = (d.flags & kVecStore) != 0;
     for (int u = gseg; u < units; u += nseg) {
         const int cb = u % ncb, run = u / ncb;
@@ -202,12 +211,18 @@ __device__ __forceinline__ void consume(const KDescB &d, int local, uint32_t *st
 }  // namespace
 
 // SINGLE: one image passed by value (nbands bands); else the batch arena.
+// Warp-specialised: the last warp produces, the others consume.  Stage s
+// has two barriers: full[s] (armed by the producer with the copy's byte
+// count, completed by the copies) and empty[s] (one arrival per consumer
+// warp once it has finished reading the stage).  The producer refills a
+// stage as soon as it is empty, so all other stages stay in flight while the
+// consumers work; no CTA-wide barrier runs inside the loop.
 template <bool SINGLE>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(kMaxBulkThreads)
 k_bulk(const BatchHeader *__restrict__ hdr, KDescB one, int nbands, int stage_words,
        int stages) {
     extern __shared__ __align__(128) uint32_t smem[];
-    __shared__ uint64_t bars[kMaxStages];
+    __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
     const KDescB *descs = SINGLE ? nullptr : reinterpret_cast<const KDescB *>(hdr + 1);
     const int G = SINGLE ? (int)gridDim.x : hdr->total_warps;
     const int64_t B = SINGLE ? nbands : hdr->total_tasks;
@@ -216,62 +231,58 @@ k_bulk(const BatchHeader *__restrict__ hdr, KDescB one, int nbands, int stage_wo
     const int b_end = (int)((B * (blockIdx.x + 1)) / G);
     if (b_begin >= b_end) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncons = (int)(blockDim.x >> 5) - 1;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], (uint32_t)ncons);
+        }
         fence_mbar_init();
     }
     __syncthreads();
 
-    int ci = 0, pi = 0;         // consumer / producer image cursors
+    int cur = 0;                 // image cursor of this warp
     if (!SINGLE) {
         const int32_t *first = reinterpret_cast<const int32_t *>(descs + hdr->n);
-        ci = pi = first[blockIdx.x];
+        cur = first[blockIdx.x];
     }
-    auto nb = [&](int i) { return descs[i].ncb * descs[i].nrb; };
-    int pb = b_begin;
-    if (warp == 0) {
-        for (int s = 0; s < stages && pb < b_end; ++s, ++pb) {
-            if (SINGLE) {
-                produce(one, pb, smem + (size_t)s * stage_words, &bars[s], lane);
-            } else {
-                while (pb >= descs[pi].band_base + nb(pi)) ++pi;
-                produce(descs[pi], pb - descs[pi].band_base, smem + (size_t)s * stage_words,
-                        &bars[s], lane);
-            }
-        }
-    }
-    bool ok = true;
-    for (int b = b_begin; b < b_end; ++b) {
-        const int it = b - b_begin;
-        const int s = it % stages;
-        if (!mbar_wait(&bars[s], (uint32_t)((it / stages) & 1))) {
-            atomicOr(&g_me_fault_flags, kFaultBulkWait);
-            ok = false;
-        }
-        // every thread takes the same decision: stop at the first failure
-        if (__syncthreads_or(!ok)) break;
-        uint32_t *stage = smem + (size_t)s * stage_words;
-        if (SINGLE) {
-            consume(one, b, stage);
+    auto image_of = [&](int b) -> KDescB {
+        if constexpr (SINGLE) {
+            return one;
         } else {
-            while (b >= descs[ci].band_base + nb(ci)) ++ci;
-            consume(descs[ci], b - descs[ci].band_base, stage);
+            while (b >= descs[cur].band_base + descs[cur].ncb * descs[cur].nrb) ++cur;
+            return descs[cur];
         }
-        __syncthreads();
-        if (warp == 0 && pb < b_end) {
-            if (SINGLE) {
-                produce(one, pb, stage, &bars[s], lane);
-            } else {
-                while (pb >= descs[pi].band_base + nb(pi)) ++pi;
-                produce(descs[pi], pb - descs[pi].band_base, stage, &bars[s], lane);
+    };
+
+    if (warp == ncons) {
+        // producer
+        for (int b = b_begin, i = 0; b < b_end; ++b, ++i) {
+            const int s = i % stages;
+            if (i >= stages && !mbar_wait(&empty[s], (uint32_t)(((i / stages) - 1) & 1))) {
+                if (lane == 0) atomicOr(&g_me_fault_flags, kFaultBulkWait);
+                break;
             }
-            ++pb;
+            const KDescB d = image_of(b);
+            produce(d, b - (SINGLE ? 0 : d.band_base), smem + (size_t)s * stage_words, &full[s],
+                    lane);
         }
-    }
-    if (!ok) {
-        // let copies already issued land before the CTA's memory goes away
-        for (int s = 0; s < stages; ++s) mbar_wait(&bars[s], 0, 1u << 16);
+    } else {
+        // consumers
+        const int nthreads = ncons * 32;
+        for (int b = b_begin, i = 0; b < b_end; ++b, ++i) {
+            const int s = i % stages;
+            if (!mbar_wait(&full[s], (uint32_t)((i / stages) & 1))) {
+                if (lane == 0) atomicOr(&g_me_fault_flags, kFaultBulkWait);
+                break;
+            }
+            const KDescB d = image_of(b);
+            consume(d, b - (SINGLE ? 0 : d.band_base), smem + (size_t)s * stage_words,
+                    (int)threadIdx.x, nthreads);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
     }
 }
 
@@ -360,7 +371,7 @@ int bulk_ctas_per_sm(const me_tile_cfg &cfg, int *out) {
     int rc = ensure_smem_attr(fn, smem);
     if (rc != ME_OK) return rc;
     int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, cfg.cta_threads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, bulk_threads(cfg), smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return record_cuda(e);
@@ -380,12 +391,12 @@ cudaError_t launch_bulk(const Geo &g, uint32_t *edge, const me_tile_cfg &cfg, cu
     DevInfo di;
     if (device_info(&di) != ME_OK) return cudaErrorInvalidDevice;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, cfg.cta_threads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bulk_threads(cfg), smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nbands, (int64_t)di.sm_count * per_sm));
-    k_bulk<true><<<grid, cfg.cta_threads, smem, s>>>(nullptr, d, (int)nbands,
+    k_bulk<true><<<grid, bulk_threads(cfg), smem, s>>>(nullptr, d, (int)nbands,
                                                      (int)(smem / cfg.stages / 4), cfg.stages);
     return cudaGetLastError();
 }

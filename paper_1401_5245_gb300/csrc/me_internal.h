@@ -13,6 +13,9 @@
 namespace me {
 
 constexpr uint32_t kAllOnes = 0xFFFFFFFFu;
+// Output columns of a register-window warp on rows wider than 32 vector
+// columns (lanes 0 and 31 only load the columns beside the block).
+constexpr int kWideLanes = 30;
 
 // What a window kernel writes per pixel word.
 enum Mode : int {
@@ -32,7 +35,7 @@ struct Geo {
     int32_t vw;                 // words per lane and row: 4 or 1
     int32_t nv;                 // vector columns written: ceil(stride / vw)
     int32_t seg_log2;           // log2 of the lanes one row segment uses
-    int32_t ncb;                // column blocks of 32 vector columns
+    int32_t ncb;                // column blocks (kWideLanes columns when nv > 32)
 };
 
 struct Outs {
@@ -126,6 +129,8 @@ void bulk_geometry(const Geo &g, const void *edge, int stage_words, KDescB *out)
 // CTAs per SM it can keep resident (after raising its smem limit).
 const void *bulk_kernel();
 size_t bulk_smem_bytes(const me_tile_cfg &cfg);
+// cta_threads consumer threads plus one producer warp.
+inline int bulk_threads(const me_tile_cfg &cfg) { return cfg.cta_threads + 32; }
 int bulk_ctas_per_sm(const me_tile_cfg &cfg, int *out);
 int regs_ctas_per_sm(const void *fn, int threads, int *out);
 // Host plan of a bulk batch arena (header, KDescB[n], first image per CTA).

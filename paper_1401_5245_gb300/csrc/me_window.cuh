@@ -2,18 +2,20 @@
 //
 // One warp tile covers RPT rows of up to 32 vector columns of VW words
 // (VW = 4: one 128-bit load per lane and row; VW = 1: one 32-bit load).
-// Narrow images fold the warp: a row segment uses nvp = 2^seg_log2 lanes
-// and the warp stacks 32 / nvp segments vertically, so every lane has work
-// whatever the width.  Each lane streams its RPT rows top to bottom: the
-// rows above, at and below the output row sit in registers, the next
-// kPrefetch rows are already requested, so each input word is loaded once
-// and kPrefetch + 3 rows are live per lane.  Horizontal neighbour words come
-// from the lanes beside it by shuffles; a lane at a segment end loads the
-// one word beyond it, or uses the outside colour.
+// Narrow rows (at most 32 vector columns) fold the warp: a row segment uses
+// nvp = 2^seg_log2 lanes and the warp stacks 32 / nvp segments vertically,
+// so every lane has work whatever the width, and the words beyond a
+// segment's ends are outside the image.  Wider rows are cut into column
+// blocks of kWideLanes columns: lanes 1..30 produce output while lanes 0 and
+// 31 only load the column just left and right of the block, so every
+// neighbour word comes from a shuffle and no lane needs extra loads.
 //
-// Outside the image (rows, words, padding bits) reads as the boundary
-// colour.  Per lane the fix-up of its VW words is precomputed as two masks,
-// applied with one three-input logic op per word: fixed = (raw & keep) | fb.
+// Each lane streams its RPT rows top to bottom: the rows above, at and below
+// the output row sit in registers and the next kPrefetch rows are already
+// requested, so each input word is loaded once per tile.  Outside the image
+// (rows, words, padding bits) reads as the boundary colour: per lane a mask
+// `keep` of its VW words' pixel bits is precomputed and each loaded word is
+// fixed with one three-input logic op, (raw & keep) | (fill & ~keep).
 //
 // Word form of the paper's steps, least significant bit = leftmost pixel:
 //   mask          M = ~I                                    (Section 3)
@@ -38,13 +40,6 @@ struct Words {
     uint32_t v[VW];
 };
 
-// A row as a lane holds it: its VW words and the words just outside them.
-template <int VW>
-struct Row {
-    Words<VW> w;
-    uint32_t hl, hr;          // raw halo words of segment-end lanes
-};
-
 // Image moved one pixel right: bit x holds pixel x-1.
 __device__ __forceinline__ uint32_t from_left(uint32_t prev, uint32_t cur) {
     return __funnelshift_l(prev, cur, 1);
@@ -54,60 +49,52 @@ __device__ __forceinline__ uint32_t from_right(uint32_t cur, uint32_t next) {
     return __funnelshift_r(cur, next, 1);
 }
 
+// Pixel bits of image word c (0 outside the row and for padding).
+__device__ __forceinline__ uint32_t col_keep(const Geo &g, int c) {
+    return (c >= 0 && c < g.nw - 1) ? kAllOnes : (c == g.nw - 1 ? g.lastmask : 0u);
+}
+
 // Per-lane constants of one tile.
 template <int VW>
 struct Lane {
-    const uint32_t *base;      // image word c0 of row 0
+    const uint32_t *base;      // image word c0 of row 0 (used only when loads)
     uint32_t *out[4];          // output word c0 of row 0, per output
-    int stride, h, nw, nvp, c0;
+    int stride, h, nvp;
     uint32_t fill;
-    uint32_t keep[VW], fb[VW]; // fixed = (raw & keep) | fb
-    uint32_t nkeep, nfb;       // the same for the word after the lane
-    bool loads;                // c0 < nw: the lane's words hold pixels
-    bool active;               // c0 < stride: the lane writes output words
-    bool seg_first, seg_last, has_prev, has_next;
+    uint32_t keep[VW];         // fixed = (raw & keep) | (fill & ~keep)
+    bool loads;                // 0 <= c0 < nw: the lane's words hold pixels
+    bool writes;               // the lane owns output words of this tile
+    bool seg_first, seg_last;  // lanes whose outer neighbour is outside
 };
 
 template <int VW>
-__device__ __forceinline__ uint32_t col_keep(const Geo &g, int c) {
-    return c < g.nw - 1 ? kAllOnes : (c == g.nw - 1 ? g.lastmask : 0u);
-}
-
-template <int VW>
 __device__ __forceinline__ Lane<VW> make_lane(const Geo &g, const Outs &o, int c0, int col,
-                                              int nvp) {
+                                              int nvp, bool owner) {
     Lane<VW> L;
-    L.base = g.img + c0;
+    L.loads = c0 >= 0 && c0 < g.nw;
+    L.writes = owner && c0 >= 0 && c0 < g.stride;
+    const int cs = c0 < 0 ? 0 : c0;            // keep pointers inside the image
+    L.base = g.img + cs;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) L.out[k] = o.p[k] ? o.p[k] + c0 : nullptr;
+    for (int k = 0; k < 4; ++k) L.out[k] = o.p[k] ? o.p[k] + cs : nullptr;
     L.stride = g.stride;
     L.h = g.h;
-    L.nw = g.nw;
     L.nvp = nvp;
-    L.c0 = c0;
     L.fill = g.fill;
 #pragma unroll
-    for (int k = 0; k < VW; ++k) {
-        L.keep[k] = col_keep<VW>(g, c0 + k);
-        L.fb[k] = g.fill & ~L.keep[k];
-    }
-    L.nkeep = col_keep<VW>(g, c0 + VW);
-    L.nfb = g.fill & ~L.nkeep;
-    L.loads = c0 < g.nw;
-    L.active = c0 < g.stride;
+    for (int k = 0; k < VW; ++k) L.keep[k] = col_keep(g, c0 + k);
     L.seg_first = (col == 0);
     L.seg_last = (col == nvp - 1);
-    L.has_prev = L.seg_first && L.loads && c0 > 0;
-    L.has_next = L.seg_last && (c0 + VW < g.nw);
     return L;
 }
 
 // Row y into registers.  CHECK: y may lie outside [0, h).
 template <int VW, bool CHECK>
-__device__ __forceinline__ Row<VW> load_row(const Lane<VW> &L, int y) {
-    Row<VW> r;
-    const bool ok = L.loads && (!CHECK || (unsigned)y < (unsigned)L.h);
-    const uint32_t *p = L.base + (size_t)y * (size_t)L.stride;
+__device__ __forceinline__ Words<VW> load_row(const Lane<VW> &L, int y) {
+    Words<VW> r;
+    const bool rowok = !CHECK || (unsigned)y < (unsigned)L.h;
+    const bool ok = L.loads && rowok;
+    const uint32_t *p = L.base + (size_t)(CHECK && !rowok ? 0 : y) * (size_t)L.stride;
     uint32_t raw[VW];
     if constexpr (VW == 4) {
         uint4 q = make_uint4(0, 0, 0, 0);
@@ -120,23 +107,20 @@ __device__ __forceinline__ Row<VW> load_row(const Lane<VW> &L, int y) {
     }
 #pragma unroll
     for (int k = 0; k < VW; ++k) {
-        const uint32_t f = (raw[k] & L.keep[k]) | L.fb[k];
-        r.w.v[k] = (!CHECK || ok || !L.loads) ? f : L.fill;
+        const uint32_t f = (raw[k] & L.keep[k]) | (L.fill & ~L.keep[k]);
+        r.v[k] = (!CHECK || rowok) ? f : L.fill;
     }
-    const bool rowok = !CHECK || (unsigned)y < (unsigned)L.h;
-    r.hl = (L.has_prev && rowok) ? __ldg(p - 1) : L.fill;
-    r.hr = (L.has_next && rowok) ? ((__ldg(p + VW) & L.nkeep) | L.nfb) : L.fill;
     return r;
 }
 
-// Words just left and right of the lane's VW words in row r.
+// Words just left and right of the lane's VW words.
 template <int VW>
-__device__ __forceinline__ void side_words(const Lane<VW> &L, const Row<VW> &r, uint32_t &prev,
-                                           uint32_t &next) {
-    const uint32_t a = __shfl_up_sync(0xFFFFFFFFu, r.w.v[VW - 1], 1, L.nvp);
-    const uint32_t b = __shfl_down_sync(0xFFFFFFFFu, r.w.v[0], 1, L.nvp);
-    prev = L.seg_first ? r.hl : a;
-    next = L.seg_last ? r.hr : b;
+__device__ __forceinline__ void side_words(const Lane<VW> &L, const Words<VW> &r,
+                                           uint32_t &prev, uint32_t &next) {
+    const uint32_t a = __shfl_up_sync(0xFFFFFFFFu, r.v[VW - 1], 1, L.nvp);
+    const uint32_t b = __shfl_down_sync(0xFFFFFFFFu, r.v[0], 1, L.nvp);
+    prev = L.seg_first ? L.fill : a;
+    next = L.seg_last ? L.fill : b;
 }
 
 template <int VW>
@@ -153,22 +137,23 @@ __device__ __forceinline__ void store_words(const Lane<VW> &L, uint32_t *out, in
     }
 }
 
-// One output row from the rows above (u), at (c) and below (d).
+// One output row from the rows above (u), at (c) and below (d); cp/cn are
+// the words beside c, up_*/dn_* beside u and d (end points only).
 template <int VW, int MODE>
-__device__ __forceinline__ void emit_row(const Lane<VW> &L, int y, const Row<VW> &u,
-                                         const Row<VW> &c, const Row<VW> &d, uint32_t cp,
+__device__ __forceinline__ void emit_row(const Lane<VW> &L, int y, const Words<VW> &u,
+                                         const Words<VW> &c, const Words<VW> &d, uint32_t cp,
                                          uint32_t cn, uint32_t up_p, uint32_t up_n,
                                          uint32_t dn_p, uint32_t dn_n) {
     uint32_t e0[VW], e1[VW], e2[VW], e3[VW];
 #pragma unroll
     for (int k = 0; k < VW; ++k) {
-        const uint32_t cur = c.w.v[k];
-        const uint32_t pv = (k == 0) ? cp : c.w.v[k - 1];
-        const uint32_t nx = (k == VW - 1) ? cn : c.w.v[k + 1];
+        const uint32_t cur = c.v[k];
+        const uint32_t pv = (k == 0) ? cp : c.v[k - 1];
+        const uint32_t nx = (k == VW - 1) ? cn : c.v[k + 1];
         const uint32_t Lw = from_left(pv, cur);         // I(x-1, y)
         const uint32_t Rw = from_right(cur, nx);        // I(x+1, y)
-        const uint32_t U = u.w.v[k];                    // I(x, y-1)
-        const uint32_t D = d.w.v[k];                    // I(x, y+1)
+        const uint32_t U = u.v[k];                      // I(x, y-1)
+        const uint32_t D = d.v[k];                      // I(x, y+1)
         const uint32_t M = ~cur;                        // the mask
         const uint32_t valid = L.keep[k];
         if constexpr (MODE == MODE_EDGE) {
@@ -184,10 +169,10 @@ __device__ __forceinline__ void emit_row(const Lane<VW> &L, int y, const Row<VW>
             // Fig. 1 neighbours 1..8 of every pixel of the word, as "is
             // white" planes; count the black ones bit-sliced and keep
             // pixels with at most one.
-            const uint32_t pu = (k == 0) ? up_p : u.w.v[k - 1];
-            const uint32_t nu = (k == VW - 1) ? up_n : u.w.v[k + 1];
-            const uint32_t pd = (k == 0) ? dn_p : d.w.v[k - 1];
-            const uint32_t nd = (k == VW - 1) ? dn_n : d.w.v[k + 1];
+            const uint32_t pu = (k == 0) ? up_p : u.v[k - 1];
+            const uint32_t nu = (k == VW - 1) ? up_n : u.v[k + 1];
+            const uint32_t pd = (k == 0) ? dn_p : d.v[k - 1];
+            const uint32_t nd = (k == VW - 1) ? dn_n : d.v[k + 1];
             const uint32_t nb[8] = {
                 from_right(U, nu),   // 1: up-right
                 U,                   // 2: up
@@ -225,14 +210,16 @@ __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, in
     const int nvp = 1 << g.seg_log2;
     const int col = lane & (nvp - 1);
     const int seg = lane >> g.seg_log2;
-    const int c0 = (cb * 32 + col) * VW;
+    const bool wide = g.nv > 32;
+    const int v = wide ? cb * kWideLanes + lane - 1 : col;
+    const bool owner = !wide || (lane >= 1 && lane <= kWideLanes);
     const int y0 = ((rb << (5 - g.seg_log2)) + seg) * RPT;
-    const Lane<VW> L = make_lane<VW>(g, o, c0, col, nvp);
-    const bool rows_left = !CHECK || y0 < g.h;    // segment has rows (uniform per segment)
+    const Lane<VW> L = make_lane<VW>(g, o, v * VW, col, nvp, owner);
+    const bool rows_left = !CHECK || y0 < g.h;    // the segment has rows
 
-    Row<VW> up = load_row<VW, CHECK>(L, y0 - 1);
-    Row<VW> cur = load_row<VW, CHECK>(L, y0);
-    Row<VW> q[kPrefetch];
+    Words<VW> up = load_row<VW, CHECK>(L, y0 - 1);
+    Words<VW> cur = load_row<VW, CHECK>(L, y0);
+    Words<VW> q[kPrefetch];
 #pragma unroll
     for (int i = 0; i < kPrefetch; ++i) q[i] = load_row<VW, CHECK>(L, y0 + 1 + i);
     uint32_t up_p = 0, up_n = 0, cur_p, cur_n;
@@ -244,11 +231,11 @@ __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, in
 #pragma unroll
         for (int j = 0; j < kPrefetch; ++j) {
             const int y = y0 + r0 + j;
-            const Row<VW> dn = q[j];
+            const Words<VW> dn = q[j];
             if (r0 + j + 1 + kPrefetch <= RPT) q[j] = load_row<VW, CHECK>(L, y + 1 + kPrefetch);
             uint32_t dn_p, dn_n;
             side_words<VW>(L, dn, dn_p, dn_n);
-            if (L.active && rows_left && (!CHECK || y < g.h))
+            if (L.writes && rows_left && (!CHECK || y < g.h))
                 emit_row<VW, MODE>(L, y, up, cur, dn, cur_p, cur_n, up_p, up_n, dn_p, dn_n);
             up = cur;
             cur = dn;
