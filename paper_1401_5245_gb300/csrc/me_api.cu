@@ -94,7 +94,9 @@ Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
     g.fill = (boundary == ME_BOUNDARY_WHITE) ? kAllOnes : 0u;
     g.vw = vw;
     g.nv = (stride + vw - 1) / vw;      // output covers the whole stride
-    g.seg_log2 = g.nv >= 32 ? 5 : ceil_log2(g.nv);
+    // narrow rows: segments of exactly nv lanes, as many as fit in a warp
+    g.seg_w = g.nv > 32 ? 32 : g.nv;
+    g.segs = 32 / g.seg_w;
     g.ncb = g.nv > 32 ? (g.nv + kWideLanes - 1) / kWideLanes : 1;
     return g;
 }

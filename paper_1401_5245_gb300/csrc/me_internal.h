@@ -34,7 +34,8 @@ struct Geo {
     uint32_t fill;              // outside colour as a word: ~0 white, 0 black
     int32_t vw;                 // words per lane and row: 4 or 1
     int32_t nv;                 // vector columns written: ceil(stride / vw)
-    int32_t seg_log2;           // log2 of the lanes one row segment uses
+    int32_t seg_w;              // lanes one row segment uses (nv, or 32 when wide)
+    int32_t segs;               // row segments stacked in one warp (32 / seg_w)
     int32_t ncb;                // column blocks (kWideLanes columns when nv > 32)
 };
 
@@ -46,9 +47,9 @@ struct Outs {
 struct BDesc {
     const uint32_t *img;
     uint32_t *edge;
-    int32_t w, h, stride, nw;
+    int32_t segs, h, stride, nw;
     uint32_t lastmask, fill;
-    int32_t vw, seg_log2, ncb, nv;
+    int32_t vw, seg_w, ncb, nv;
     int32_t task_base, ntasks;
 };
 static_assert(sizeof(BDesc) == 64, "BDesc is 64 bytes");
@@ -73,8 +74,9 @@ constexpr int32_t kBulkCopy = 1;    // copy with cp.async.bulk (16-byte rows)
 constexpr int32_t kVecStore = 2;    // 128-bit stores allowed
 constexpr int32_t kRowMode = 4;     // full rows, one contiguous copy per band
 
-// Device arena of one batch: header, then descriptors, then the first task
-// of every warp's contiguous task range.
+// Device arena of one batch: header, then descriptors, then per work owner
+// (warp or CTA) the image of its first unit and (register window) its first
+// task; owner w runs tasks [first_task[w], first_task[w + 1]).
 struct BatchHeader {
     int32_t n;
     int32_t total_tasks;
@@ -85,9 +87,11 @@ struct BatchHeader {
 };
 static_assert(sizeof(BatchHeader) == 256, "BatchHeader is 256 bytes");
 
+__host__ __device__ inline size_t owner_table_bytes(int owners) {
+    return (((size_t)owners + 1) * sizeof(int32_t) + 255) / 256 * 256;
+}
 inline size_t arena_bytes(int n, int total_warps) {
-    return sizeof(BatchHeader) + (size_t)n * sizeof(BDesc) +
-           (((size_t)total_warps + 1) * sizeof(int32_t) + 255) / 256 * 256;
+    return sizeof(BatchHeader) + (size_t)n * sizeof(BDesc) + 2 * owner_table_bytes(total_warps);
 }
 
 // ---------------------------------------------------------------- helpers

@@ -48,8 +48,8 @@ static WindowFn pick_mode(int mode, int rpt) {
     }
 }
 
-static int64_t tasks_of(int h, int seg_log2, int ncb, int rpt) {
-    const int64_t rows_per_task = (int64_t)rpt << (5 - seg_log2);
+static int64_t tasks_of(int h, int segs, int ncb, int rpt) {
+    const int64_t rows_per_task = (int64_t)rpt * segs;
     const int64_t nrb = (h + rows_per_task - 1) / rows_per_task;
     return (int64_t)ncb * nrb;
 }
@@ -59,7 +59,7 @@ cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
     WindowFn fn = (g.vw == 4) ? pick_mode<4>(mode, cfg.rows_per_lane)
                               : pick_mode<1>(mode, cfg.rows_per_lane);
     if (fn == nullptr) return cudaErrorInvalidValue;
-    const int64_t ntasks = tasks_of(g.h, g.seg_log2, g.ncb, cfg.rows_per_lane);
+    const int64_t ntasks = tasks_of(g.h, g.segs, g.ncb, cfg.rows_per_lane);
     if (ntasks > INT32_MAX) return cudaErrorInvalidValue;
     const int threads = cfg.cta_threads;
     const int warps_per_cta = threads / 32;
@@ -81,28 +81,29 @@ cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
 // ------------------------------------------------------------- batch
 // Every warp owns a contiguous range of the batch's tiles, so consecutive
 // tiles of one warp are usually vertically adjacent in the same image and
-// the halo rows it re-reads are still in L1/L2.  The host writes the image
-// holding each warp's first tile; the warp then walks forward.
+// the halo rows it re-reads are still in L1/L2.  The host gives every warp
+// the same number of tiles and writes each warp's first tile and its image;
+// the warp then walks forward.
 template <int RPT>
 __global__ void __launch_bounds__(512)
 k_batch(const BatchHeader *__restrict__ hdr) {
     const BDesc *descs = reinterpret_cast<const BDesc *>(hdr + 1);
-    const int32_t *warp_first_image =
-        reinterpret_cast<const int32_t *>(descs + hdr->n);
+    const int W = hdr->total_warps;
+    const int32_t *warp_first_image = reinterpret_cast<const int32_t *>(descs + hdr->n);
+    const int32_t *warp_first_task = reinterpret_cast<const int32_t *>(
+        reinterpret_cast<const char *>(warp_first_image) + owner_table_bytes(W));
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int W = hdr->total_warps;
     if (warp >= W) return;
-    const int64_t T = hdr->total_tasks;
-    const int t0 = (int)((T * warp) / W);
-    const int t1 = (int)((T * (warp + 1)) / W);
+    const int t0 = warp_first_task[warp];
+    const int t1 = warp_first_task[warp + 1];
     int i = warp_first_image[warp];
     for (int t = t0; t < t1; ++t) {
         while (t >= descs[i].task_base + descs[i].ntasks) ++i;
         const BDesc &d = descs[i];
         Geo g;
         g.img = d.img;
-        g.w = d.w;
+        g.w = 0;
         g.h = d.h;
         g.stride = d.stride;
         g.nw = d.nw;
@@ -110,7 +111,8 @@ k_batch(const BatchHeader *__restrict__ hdr) {
         g.fill = d.fill;
         g.vw = d.vw;
         g.nv = d.nv;
-        g.seg_log2 = d.seg_log2;
+        g.seg_w = d.seg_w;
+        g.segs = d.segs;
         g.ncb = d.ncb;
         Outs o;
         o.p[0] = d.edge;
@@ -172,14 +174,14 @@ static void fill_bdesc(const me_desc &d, const me_tile_cfg &cfg, BDesc *out) {
     Geo g = make_geo(d.img, d.w, d.h, d.stride_words, d.boundary, vw);
     out->img = d.img;
     out->edge = d.edge;
-    out->w = g.w;
+    out->segs = g.segs;
     out->h = g.h;
     out->stride = g.stride;
     out->nw = g.nw;
     out->lastmask = g.lastmask;
     out->fill = g.fill;
     out->vw = g.vw;
-    out->seg_log2 = g.seg_log2;
+    out->seg_w = g.seg_w;
     out->ncb = g.ncb;
     out->nv = g.nv;
 }
@@ -193,7 +195,7 @@ int batch_tasks(const me_desc *descs, int n, const me_tile_cfg &cfg,
         if (rc != ME_OK) return rc;
         BDesc b;
         fill_bdesc(d, cfg, &b);
-        total += tasks_of(b.h, b.seg_log2, b.ncb, cfg.rows_per_lane);
+        total += tasks_of(b.h, b.segs, b.ncb, cfg.rows_per_lane);
     }
     *total_tasks = total;
     return total > INT32_MAX ? ME_ERR_ARG : ME_OK;
@@ -203,7 +205,9 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
                int total_warps, void *host_arena, int *bad) {
     BatchHeader *hdr = static_cast<BatchHeader *>(host_arena);
     BDesc *bd = reinterpret_cast<BDesc *>(hdr + 1);
-    int32_t *first = reinterpret_cast<int32_t *>(bd + n);
+    int32_t *first_image = reinterpret_cast<int32_t *>(bd + n);
+    int32_t *first_task = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(first_image) +
+                                                      owner_table_bytes(total_warps));
     std::memset(hdr, 0, sizeof(*hdr));
     int64_t total = 0, bytes = 0;
     for (int i = 0; i < n; ++i) {
@@ -214,7 +218,7 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
             return rc;
         }
         fill_bdesc(d, cfg, &bd[i]);
-        const int64_t nt = tasks_of(bd[i].h, bd[i].seg_log2, bd[i].ncb, cfg.rows_per_lane);
+        const int64_t nt = tasks_of(bd[i].h, bd[i].segs, bd[i].ncb, cfg.rows_per_lane);
         if (total + nt > INT32_MAX) {
             if (bad) *bad = i;
             return ME_ERR_ARG;
@@ -229,14 +233,17 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
     hdr->total_warps = total_warps;
     hdr->rows_per_lane = cfg.rows_per_lane;
     hdr->bytes = bytes;
-    // image of each warp's first tile (two pointers, both increasing)
-    int i = 0;
-    for (int w = 0; w < total_warps; ++w) {
-        const int64_t t0 = (total * w) / total_warps;
-        while (i < n - 1 && t0 >= (int64_t)bd[i].task_base + bd[i].ntasks) ++i;
-        first[w] = i;
+    // Equal numbers of tiles per warp.  A tile costs about one memory round
+    // trip whatever its width, so equal counts finish together better than
+    // equal bytes (measured on the uneven 4096-image batch).
+    for (int w = 0; w <= total_warps; ++w)
+        first_task[w] = (int32_t)((total * w) / total_warps);
+    // the image holding each warp's first tile (both sequences increase)
+    int k = 0;
+    for (int w = 0; w <= total_warps; ++w) {
+        while (k < n - 1 && first_task[w] >= bd[k].task_base + bd[k].ntasks) ++k;
+        first_image[w] = k;
     }
-    first[total_warps] = n > 0 ? n - 1 : 0;
     return ME_OK;
 }
 

@@ -3,9 +3,9 @@
 // One warp tile covers RPT rows of up to 32 vector columns of VW words
 // (VW = 4: one 128-bit load per lane and row; VW = 1: one 32-bit load).
 // Narrow rows (at most 32 vector columns) fold the warp: a row segment uses
-// nvp = 2^seg_log2 lanes and the warp stacks 32 / nvp segments vertically,
-// so every lane has work whatever the width, and the words beyond a
-// segment's ends are outside the image.  Wider rows are cut into column
+// exactly as many lanes as the row has vector columns and the warp stacks
+// 32 / seg_w segments vertically, so nearly every lane has work whatever
+// the width, and the words beyond a segment's ends are outside the image.  Wider rows are cut into column
 // blocks of kWideLanes columns: lanes 1..30 produce output while lanes 0 and
 // 31 only load the column just left and right of the block, so every
 // neighbour word comes from a shuffle and no lane needs extra loads.
@@ -113,12 +113,14 @@ __device__ __forceinline__ Words<VW> load_row(const Lane<VW> &L, int y) {
     return r;
 }
 
-// Words just left and right of the lane's VW words.
+// Words just left and right of the lane's VW words.  Segments sit side by
+// side in the warp, so the lane before / after is in the same segment
+// unless this lane is a segment end, whose outer neighbour is outside.
 template <int VW>
 __device__ __forceinline__ void side_words(const Lane<VW> &L, const Words<VW> &r,
                                            uint32_t &prev, uint32_t &next) {
-    const uint32_t a = __shfl_up_sync(0xFFFFFFFFu, r.v[VW - 1], 1, L.nvp);
-    const uint32_t b = __shfl_down_sync(0xFFFFFFFFu, r.v[0], 1, L.nvp);
+    const uint32_t a = __shfl_up_sync(0xFFFFFFFFu, r.v[VW - 1], 1);
+    const uint32_t b = __shfl_down_sync(0xFFFFFFFFu, r.v[0], 1);
     prev = L.seg_first ? L.fill : a;
     next = L.seg_last ? L.fill : b;
 }
@@ -207,14 +209,15 @@ template <int VW, int RPT, int MODE, bool CHECK>
 __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, int cb, int rb,
                                                  int lane) {
     static_assert(RPT % kPrefetch == 0, "rows per lane is a multiple of the prefetch");
-    const int nvp = 1 << g.seg_log2;
-    const int col = lane & (nvp - 1);
-    const int seg = lane >> g.seg_log2;
+    // lane -> (segment, column): (lane + 0.5) / seg_w is never within float
+    // rounding of an integer, so truncation gives the exact quotient
+    const int seg = (int)(((float)lane + 0.5f) * __frcp_rn((float)g.seg_w));
+    const int col = lane - seg * g.seg_w;
     const bool wide = g.nv > 32;
     const int v = wide ? cb * kWideLanes + lane - 1 : col;
-    const bool owner = !wide || (lane >= 1 && lane <= kWideLanes);
-    const int y0 = ((rb << (5 - g.seg_log2)) + seg) * RPT;
-    const Lane<VW> L = make_lane<VW>(g, o, v * VW, col, nvp, owner);
+    const bool owner = seg < g.segs && (!wide || (lane >= 1 && lane <= kWideLanes));
+    const int y0 = (rb * g.segs + seg) * RPT;
+    const Lane<VW> L = make_lane<VW>(g, o, seg < g.segs ? v * VW : -VW, col, g.seg_w, owner);
     const bool rows_left = !CHECK || y0 < g.h;    // the segment has rows
 
     Words<VW> up = load_row<VW, CHECK>(L, y0 - 1);
@@ -250,7 +253,7 @@ __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, in
 template <int VW, int RPT, int MODE>
 __device__ __forceinline__ void window_tile(const Geo &g, const Outs &o, int cb, int rb,
                                             int lane) {
-    const int rows_per_task = RPT << (5 - g.seg_log2);
+    const int rows_per_task = RPT * g.segs;
     const int top = rb * rows_per_task;
     if (top >= 1 && top + rows_per_task < g.h)
         window_tile_rows<VW, RPT, MODE, false>(g, o, cb, rb, lane);
