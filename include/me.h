@@ -218,6 +218,39 @@ int64_t me_batch_plan_bytes(const me_batch_plan *plan);
 /* Waits for the plan's uploads, then frees it.  NULL is ignored. */
 int me_batch_plan_destroy(me_batch_plan *plan);
 
+/*
+ * A batch that lives in HOST memory, end to end: every image is a range of
+ * one host input buffer and its edge map goes to the same range of one host
+ * output buffer (a ragged batch, as a serving front end or a file reader
+ * lays it out).
+ *
+ * host_in, host_out  host buffers; pinned memory (cudaHostAlloc,
+ *                    cudaHostRegister, torch pin_memory) moves at full link
+ *                    speed, pageable memory works through the driver's
+ *                    staging.  They must not overlap.
+ * imgs[i]            offset_words: where image i starts in both buffers (16-
+ *                    byte aligned offsets keep the 128-bit path); the image
+ *                    takes h * stride_words words from there; w, h,
+ *                    stride_words, boundary as me_desc.
+ * chunk_bytes        input bytes per pipeline chunk (0: 32 MiB); images are
+ *                    grouped into chunks in order, at least one per chunk.
+ * stream             the work starts after what `stream` already holds.
+ *
+ * The library copies chunk k+1 up, computes chunk k (one persistent batch
+ * launch) and copies chunk k-1 down at the same time, on its own streams,
+ * into device staging it owns (three chunk slots of input and output,
+ * kept until me_shutdown).
+ * Synchronous: returns when every edge map is in host_out.
+ */
+typedef struct me_host_image {
+    int64_t offset_words;
+    int32_t w, h, stride_words, boundary;
+} me_host_image;
+
+int me_edges_batch_host(const uint32_t *host_in, uint32_t *host_out,
+                        const me_host_image *imgs, int32_t n, int64_t chunk_bytes,
+                        me_stream_t stream);
+
 /* ---- tile configuration and autotuning --------------------------------- */
 
 #define ME_KIND_SINGLE 0     /* me_edges and its single-image relatives */

@@ -61,6 +61,11 @@ class me_tile_cfg(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class me_host_image(ctypes.Structure):
+    _fields_ = [("offset_words", c_i64), ("w", c_i32), ("h", c_i32),
+                ("stride_words", c_i32), ("boundary", c_i32)]
+
+
 class me_serve_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", c_i64), ("staging_bytes", c_i64),
                 ("max_inflight", c_i32), ("max_batch", c_i32), ("tick_us", c_i32),
@@ -91,6 +96,8 @@ PROTOTYPES = {
     "me_batch_run": (ctypes.c_int, [c_vp, c_vp]),
     "me_batch_plan_bytes": (c_i64, [c_vp]),
     "me_batch_plan_destroy": (ctypes.c_int, [c_vp]),
+    "me_edges_batch_host": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(me_host_image), c_i32,
+                                           c_i64, c_vp]),
     "me_get_tile_cfg": (ctypes.c_int, [c_i32, ctypes.POINTER(me_tile_cfg)]),
     "me_set_tile_cfg": (ctypes.c_int, [c_i32, ctypes.POINTER(me_tile_cfg)]),
     "me_autotune": (ctypes.c_int, [c_i32, ctypes.POINTER(me_desc), c_i32, c_i32, c_vp,
@@ -202,6 +209,28 @@ def make_descs(items) -> ctypes.Array:
 def me_edges_batch(descs, n=None, stream=None) -> int:
     n = len(descs) if n is None else n
     return load().me_edges_batch(descs, n, stream_handle(stream))
+
+
+def make_host_images(items) -> ctypes.Array:
+    """items: iterable of (offset_words, w, h, stride_words, boundary)."""
+    items = list(items)
+    arr = (me_host_image * max(1, len(items)))()
+    for i, (off, w, h, stride, boundary) in enumerate(items):
+        arr[i] = me_host_image(off, w, h, stride, boundary)
+    return arr
+
+
+def me_edges_batch_host(host_in, host_out, imgs, n=None, chunk_bytes=0, stream=None) -> int:
+    """host_in / host_out: numpy arrays, pinned torch CPU tensors or pointers."""
+    def hptr(x):
+        if hasattr(x, "ctypes"):
+            return x.ctypes.data
+        if hasattr(x, "data_ptr"):
+            return x.data_ptr()
+        return int(x)
+    n = len(imgs) if n is None else n
+    return load().me_edges_batch_host(hptr(host_in), hptr(host_out), imgs, n, chunk_bytes,
+                                      stream_handle(stream))
 
 
 class BatchPlan:

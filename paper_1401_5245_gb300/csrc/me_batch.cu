@@ -44,14 +44,9 @@ int fail(cudaError_t e) {
     return record_cuda(e);
 }
 
-// How one batch launches under a configuration.
-struct Setup {
-    me_tile_cfg cfg;
-    int grid = 0, threads = 0;
-    size_t smem = 0, arena = 0;
-    const void *fn = nullptr;
-    int stage_words = 0;
-};
+}  // namespace
+
+using Setup = BatchSetup;
 
 int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, Setup *s) {
     int64_t units = 0;
@@ -91,6 +86,20 @@ int fill_arena(const me_desc *descs, int n, const Setup &s, void *host) {
     int bad = -1;
     return plan_batch(descs, n, s.cfg, s.grid * (s.threads / 32), host, &bad);
 }
+
+cudaError_t launch_planned(const Setup &s, void *arena_dev, cudaStream_t stream) {
+    void *arena = arena_dev;
+    KDescB none = {};
+    int zero = 0, stage_words = s.stage_words, stages = s.cfg.stages;
+    void *regs_args[] = {&arena};
+    void *bulk_args[] = {&arena, &none, &zero, &stage_words, &stages};
+    cudaError_t e = cudaLaunchKernel(s.fn, dim3(s.grid), dim3(s.threads),
+                                     s.cfg.engine == ME_ENGINE_BULK ? bulk_args : regs_args,
+                                     s.smem, stream);
+    return e;
+}
+
+namespace {
 
 // Kernel node of the batch kernel reading the arena at `dev`.
 cudaError_t add_kernel_node(cudaGraph_t g, const cudaGraphNode_t *dep, size_t ndep,
@@ -342,6 +351,9 @@ int me_batch_plan_destroy(me_batch_plan *plan) {
     return ME_OK;
 }
 
-int me_shutdown(void) { return batch_shutdown_all(); }
+int me_shutdown(void) {
+    host_pipes_shutdown();
+    return batch_shutdown_all();
+}
 
 }  // extern "C"

@@ -370,14 +370,7 @@ int bulk_ctas_per_sm(const me_tile_cfg &cfg, int *out) {
     const size_t smem = bulk_smem_bytes(cfg);
     int rc = ensure_smem_attr(fn, smem);
     if (rc != ME_OK) return rc;
-    int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, bulk_threads(cfg), smem);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return record_cuda(e);
-    }
-    *out = n;
-    return ME_OK;
+    return cached_occupancy(fn, bulk_threads(cfg), smem, out);
 }
 
 cudaError_t launch_bulk(const Geo &g, uint32_t *edge, const me_tile_cfg &cfg, cudaStream_t s) {
@@ -391,8 +384,8 @@ cudaError_t launch_bulk(const Geo &g, uint32_t *edge, const me_tile_cfg &cfg, cu
     DevInfo di;
     if (device_info(&di) != ME_OK) return cudaErrorInvalidDevice;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bulk_threads(cfg), smem);
-    if (e != cudaSuccess) return e;
+    if (cached_occupancy(fn, bulk_threads(cfg), smem, &occ) != ME_OK)
+        return cudaErrorInvalidValue;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, occ) : occ;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nbands, (int64_t)di.sm_count * per_sm));

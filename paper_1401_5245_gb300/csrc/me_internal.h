@@ -137,6 +137,8 @@ size_t bulk_smem_bytes(const me_tile_cfg &cfg);
 inline int bulk_threads(const me_tile_cfg &cfg) { return cfg.cta_threads + 32; }
 int bulk_ctas_per_sm(const me_tile_cfg &cfg, int *out);
 int regs_ctas_per_sm(const void *fn, int threads, int *out);
+// CTAs of `fn` that fit on one SM (cached per device, kernel, size).
+int cached_occupancy(const void *fn, int threads, size_t smem, int *out);
 // Host plan of a bulk batch arena (header, KDescB[n], first image per CTA).
 int plan_batch_bulk(const me_desc *descs, int n, const me_tile_cfg &cfg, int grid,
                     void *host_arena, int64_t *total_bands);
@@ -160,6 +162,21 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
 int batch_tasks(const me_desc *descs, int n, const me_tile_cfg &cfg,
                 int64_t *total_tasks);
 
+// How one batch launches under a tile configuration: grid, threads,
+// dynamic shared memory, arena size and kernel.
+struct BatchSetup {
+    me_tile_cfg cfg;
+    int grid = 0, threads = 0;
+    size_t smem = 0, arena = 0;
+    const void *fn = nullptr;
+    int stage_words = 0;
+};
+int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, BatchSetup *s);
+// Write the arena of a batch (s.arena bytes) into host memory.
+int fill_arena(const me_desc *descs, int n, const BatchSetup &s, void *host);
+// Launch the batch kernel over an arena already in device memory.
+cudaError_t launch_planned(const BatchSetup &s, void *arena_dev, cudaStream_t stream);
+
 // A ring of batch launch slots (pinned staging, device arena, cached
 // graphs).  launch() is thread-safe; a slot is reused only after its last
 // launch completed (waits for it if needed).
@@ -179,6 +196,9 @@ class BatchRing {
     Slot *slots_;
     std::mutex mu_;
 };
+
+// Release the host-batch pipelines (streams, device slots) on every device.
+int host_pipes_shutdown();
 
 // The five staged passes.
 cudaError_t launch_staged(const Geo &g, uint32_t *mask, uint32_t *edge,

@@ -2,6 +2,9 @@
 // per launch (all output modes) and the persistent batch kernel.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "me_internal.h"
 #include "me_window.cuh"
@@ -140,12 +143,42 @@ static BatchFn pick_batch(int rpt) {
 }
 
 int regs_ctas_per_sm(const void *fn, int threads, int *out) {
+    return cached_occupancy(fn, threads, 0, out);
+}
+
+int cached_occupancy(const void *fn, int threads, size_t smem, int *out) {
+    // cudaOccupancyMaxActiveBlocksPerMultiprocessor costs microseconds per
+    // call; launches ask it every time, so remember answers per device
+    struct Key {
+        const void *fn;
+        int threads, dev;
+        size_t smem;
+        bool operator==(const Key &o) const {
+            return fn == o.fn && threads == o.threads && dev == o.dev && smem == o.smem;
+        }
+    };
+    static std::mutex mu;
+    static std::vector<std::pair<Key, int>> seen;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return record_cuda(e);
+    const Key k{fn, threads, dev, smem};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &kv : seen)
+            if (kv.first == k) {
+                *out = kv.second;
+                return ME_OK;
+            }
+    }
     int n = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return record_cuda(e);
     }
+    std::lock_guard<std::mutex> lk(mu);
+    seen.push_back({k, n});
     *out = n;
     return ME_OK;
 }

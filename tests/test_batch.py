@@ -182,3 +182,69 @@ def test_zero_and_bad_batches():
     bad = list(items)
     bad[1] = (bad[1][0], bad[1][1], bad[1][2], bad[1][3], 0, 0)   # stride 0
     assert _lib.me_edges_batch(_lib.make_descs(bad), 3) == _lib.C["ME_ERR_ARG"]
+
+
+# ------------------------------------------------------- batch in host memory
+def host_batch(seed, n, lo, hi, gap_words=0, align4=True):
+    """Images packed one after another in one host buffer (optionally with
+    gaps), as me_edges_batch_host takes them."""
+    shapes = S.batch_shapes(seed, n, lo, hi)
+    imgs, items, off = [], [], 0
+    for i, (w, h) in enumerate(shapes):
+        img = S.strokes(w, h, max(1, (w * h) // 3000), seed * 31 + i)
+        stride = S.batch_stride(w, pad16=align4)
+        words = S.pack(img, stride, pad="random", seed=i)
+        imgs.append((img, words, off))
+        items.append((off, w, h, stride, i % 2))
+        off += words.size + gap_words
+        if align4:
+            off = (off + 3) // 4 * 4
+    buf = np.full(off + 16, SENTINEL, dtype=np.uint32)
+    for img, words, o in imgs:
+        buf[o:o + words.size] = words.ravel()
+    return imgs, items, buf
+
+
+def check_host(imgs, items, out):
+    covered = np.zeros(out.size, dtype=bool)
+    for (img, words, o), it in zip(imgs, items):
+        h, w = img.shape
+        ow = out[o:o + words.size].reshape(words.shape)
+        check_output_layout(ow, w)
+        assert np.array_equal(S.unpack(ow, w), O.edges(img, it[4])), (w, h)
+        covered[o:o + words.size] = True
+    assert (out[~covered] == SENTINEL).all(), "bytes between images were written"
+
+
+@pytest.mark.parametrize("chunk", [0, 1 << 20, 64 << 10])
+def test_host_batch_chunks(chunk):
+    imgs, items, buf = host_batch(20, 120, 1, 1500)
+    out = np.full_like(buf, SENTINEL)
+    rc = _lib.me_edges_batch_host(buf, out, _lib.make_host_images(items), len(items), chunk)
+    assert rc == 0, _lib.status_string(rc)
+    check_host(imgs, items, out)
+
+
+def test_host_batch_gaps_unaligned_and_pinned():
+    import torch
+    imgs, items, buf = host_batch(21, 60, 1, 900, gap_words=5, align4=False)
+    pin_in = torch.from_numpy(buf.view(np.int32)).pin_memory()
+    pin_out = torch.full_like(pin_in, int(np.uint32(SENTINEL).view(np.int32))).pin_memory()
+    rc = _lib.me_edges_batch_host(pin_in, pin_out, _lib.make_host_images(items), len(items),
+                                  256 << 10)
+    assert rc == 0, _lib.status_string(rc)
+    check_host(imgs, items, pin_out.numpy().view(np.uint32))
+    assert _lib.me_device_faults(clear=True) == 0
+
+
+def test_host_batch_errors():
+    imgs, items, buf = host_batch(22, 4, 16, 64)
+    L = _lib.load()
+    descs = _lib.make_host_images(items)
+    assert L.me_edges_batch_host(buf.ctypes.data, buf.ctypes.data, descs, 4, 0, None) == \
+        _lib.C["ME_ERR_ALIAS"]
+    bad = _lib.make_host_images([(-4,) + tuple(items[0][1:])])
+    out = np.empty_like(buf)
+    assert L.me_edges_batch_host(buf.ctypes.data, out.ctypes.data, bad, 1, 0, None) == \
+        _lib.C["ME_ERR_ARG"]
+    assert L.me_edges_batch_host(None, None, None, 0, 0, None) == 0
