@@ -188,7 +188,7 @@ typedef struct me_desc {
 
 /*
  * me_edges on n images of any sizes in ONE persistent kernel launch,
- * replayed from a captured CUDA graph.  descs is a HOST array, copied
+ * replayed from a CUDA graph.  descs is a HOST array, copied
  * before the call returns (the caller may reuse it at once).  Image and
  * edge buffers are caller-owned device memory, checked for NULL, size and
  * overlap within each descriptor but not against one another: two
@@ -280,10 +280,11 @@ int me_set_tile_cfg(int32_t kind, const me_tile_cfg *cfg);
 /*
  * Time every candidate configuration on the caller's images (device
  * buffers; results are written to their edge buffers) with CUDA events on
- * `stream`, set the fastest for `kind`, and return it in *best.  Runs
- * synchronously.  If the environment variable ME_TUNE_CACHE names a file,
- * the choice is also written there and read back by the next process
- * (keyed by device name and kind).  `reps` timed repetitions per candidate.
+ * `stream`, set the fastest for `kind`, and return it in *best.  Each
+ * candidate runs `reps` calls back to back (steady-state throughput), best
+ * of three such runs.  Runs synchronously.  If the environment variable
+ * ME_TUNE_CACHE names a file, the choice is also written there and read
+ * back by the next process (keyed by device name and kind).
  */
 int me_autotune(int32_t kind, const me_desc *sample, int32_t n, int32_t reps,
                 me_stream_t stream, me_tile_cfg *best);

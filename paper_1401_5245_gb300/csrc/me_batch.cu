@@ -2,15 +2,16 @@
 // replayed from CUDA graphs.
 //
 // A launch plans the batch on the host (descriptors, each work owner's first
-// image), writes the plan into a pinned staging slot and launches that
-// slot's graph: one memcpy node (staging -> device arena) and one kernel
-// node (the persistent batch kernel of the configured engine reading the
-// arena).  Slots form a ring (BatchRing); a slot is reused only after the
-// event recorded behind its last launch has completed, so graphs in flight
-// never see their staging or arena overwritten.  Graphs are cached per
-// slot, keyed by the tile configuration and grid; the memcpy node's size is
-// set per launch.  me_edges_batch uses one ring per device; a server owns
-// its own ring.
+// image), writes the plan into a pinned staging slot, uploads it to the
+// slot's device arena on the ring's own copy stream (so the upload overlaps
+// the previous batch's kernel), and launches the slot's graph on the
+// caller's stream once the upload is done: one kernel node, the persistent
+// batch kernel of the configured engine reading the arena.  Slots form a
+// ring (BatchRing); a slot is reused only after the event recorded behind
+// its last launch has completed, so kernels in flight never see their
+// staging or arena overwritten.  Graphs are cached per slot, keyed by the
+// tile configuration and grid.  me_edges_batch uses one ring per device; a
+// server owns its own ring.
 #include <algorithm>
 #include <cstring>
 #include <memory>
@@ -30,7 +31,6 @@ constexpr size_t kMinSlot = 64 * 1024;
 struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t copy = nullptr;
 };
 
 size_t round_pow2(size_t v) {
@@ -118,16 +118,13 @@ cudaError_t add_kernel_node(cudaGraph_t g, const cudaGraphNode_t *dep, size_t nd
     return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
 }
 
-// Graph: copy the arena host -> device, then the persistent kernel.
-cudaError_t build_graph(const void *host, void *dev, size_t bytes, const Setup &s,
-                        GraphEntry *out) {
+// Graph: the persistent kernel reading the arena at `dev`.
+cudaError_t build_graph(void *dev, const Setup &s, GraphEntry *out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return e;
-    cudaGraphNode_t copy = nullptr, kern = nullptr;
-    e = cudaGraphAddMemcpyNode1D(&copy, g, nullptr, 0, dev, host, bytes,
-                                 cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = add_kernel_node(g, &copy, 1, s, dev, &kern);
+    cudaGraphNode_t kern = nullptr;
+    e = add_kernel_node(g, nullptr, 0, s, dev, &kern);
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
     if (e != cudaSuccess) {
@@ -136,7 +133,6 @@ cudaError_t build_graph(const void *host, void *dev, size_t bytes, const Setup &
     }
     out->graph = g;
     out->exec = exec;
-    out->copy = copy;
     return cudaSuccess;
 }
 
@@ -147,7 +143,8 @@ struct BatchRing::Slot {
     size_t cap = 0;
     void *host = nullptr;
     void *dev = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done = nullptr;        // behind the kernel that read the arena
+    cudaEvent_t copied = nullptr;      // behind the arena's upload
     bool pending = false;
     std::unordered_map<uint64_t, GraphEntry> graphs;
 
@@ -165,8 +162,9 @@ struct BatchRing::Slot {
         if (host) cudaFreeHost(host);
         if (dev) cudaFree(dev);
         if (done) cudaEventDestroy(done);
+        if (copied) cudaEventDestroy(copied);
         host = dev = nullptr;
-        done = nullptr;
+        done = copied = nullptr;
         cap = 0;
     }
     int reserve(size_t need) {
@@ -183,8 +181,8 @@ struct BatchRing::Slot {
             release();
             return fail(e);
         }
-        if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess) {
-            done = nullptr;
+        if ((e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming)) != cudaSuccess) {
             release();
             return fail(e);
         }
@@ -203,6 +201,8 @@ BatchRing::~BatchRing() {
 void BatchRing::release() {
     std::lock_guard<std::mutex> lk(mu_);
     for (int i = 0; i < n_; ++i) slots_[i].release();
+    if (copy_) cudaStreamDestroy(copy_);
+    copy_ = nullptr;
 }
 
 int BatchRing::launch(const me_desc *descs, int n, cudaStream_t stream) {
@@ -221,18 +221,27 @@ int BatchRing::launch(const me_desc *descs, int n, cudaStream_t stream) {
     }
     if ((rc = slot.reserve(su.arena)) != ME_OK) return rc;
     if ((rc = fill_arena(descs, n, su, slot.host)) != ME_OK) return rc;
+    if (copy_ == nullptr &&
+        (e = cudaStreamCreateWithFlags(&copy_, cudaStreamNonBlocking)) != cudaSuccess) {
+        copy_ = nullptr;
+        return fail(e);
+    }
     const uint64_t key = cfg_key(su.cfg) * 31 + (uint64_t)su.grid;
     auto it = slot.graphs.find(key);
     if (it == slot.graphs.end()) {
         GraphEntry ge;
-        if ((e = build_graph(slot.host, slot.dev, slot.cap, su, &ge)) != cudaSuccess)
-            return fail(e);
+        if ((e = build_graph(slot.dev, su, &ge)) != cudaSuccess) return fail(e);
         it = slot.graphs.emplace(key, ge).first;
     }
-    // copy only what this batch filled
-    e = cudaGraphExecMemcpyNodeSetParams1D(it->second.exec, it->second.copy, slot.dev,
-                                           slot.host, su.arena, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return fail(e);
+    // The plan goes up on the ring's own copy stream, so it overlaps
+    // whatever `stream` is still running (the previous batch's kernel); the
+    // kernel waits for it.  The slot's arena and staging are free: the
+    // slot's last kernel has finished (waited for above).
+    if ((e = cudaMemcpyAsync(slot.dev, slot.host, su.arena, cudaMemcpyHostToDevice, copy_)) !=
+        cudaSuccess)
+        return fail(e);
+    if ((e = cudaEventRecord(slot.copied, copy_)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamWaitEvent(stream, slot.copied, 0)) != cudaSuccess) return fail(e);
     if ((e = cudaGraphLaunch(it->second.exec, stream)) != cudaSuccess) return fail(e);
     if ((e = cudaEventRecord(slot.done, stream)) != cudaSuccess) return fail(e);
     slot.pending = true;

@@ -194,6 +194,7 @@ class BatchRing {
     int n_;
     int next_ = 0;
     Slot *slots_;
+    cudaStream_t copy_ = nullptr;   // uploads plans beside the caller's stream
     std::mutex mu_;
 };
 

@@ -11,7 +11,7 @@
 // neighbour word comes from a shuffle and no lane needs extra loads.
 //
 // Each lane streams its RPT rows top to bottom: the rows above, at and below
-// the output row sit in registers and the next kPrefetch rows are already
+// the output row sit in registers and the next prefetch_rows(RPT) rows are already
 // requested, so each input word is loaded once per tile.  Outside the image
 // (rows, words, padding bits) reads as the boundary colour: per lane a mask
 // `keep` of its VW words' pixel bits is precomputed and each loaded word is
@@ -32,8 +32,9 @@
 
 namespace me {
 
-// Rows requested ahead of the one being computed; RPT is a multiple of it.
-constexpr int kPrefetch = 4;
+// Rows requested ahead of the one being computed: all of a tile's rows up
+// to 8 rows per lane (one memory round trip per tile), else 4 at a time.
+__host__ __device__ constexpr int prefetch_rows(int rpt) { return rpt <= 8 ? rpt : 4; }
 
 template <int VW>
 struct Words {
@@ -208,7 +209,8 @@ __device__ __forceinline__ void emit_row(const Lane<VW> &L, int y, const Words<V
 template <int VW, int RPT, int MODE, bool CHECK>
 __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, int cb, int rb,
                                                  int lane) {
-    static_assert(RPT % kPrefetch == 0, "rows per lane is a multiple of the prefetch");
+    constexpr int PF = prefetch_rows(RPT);
+    static_assert(RPT % PF == 0, "rows per lane is a multiple of the prefetch");
     // lane -> (segment, column): (lane + 0.5) / seg_w is never within float
     // rounding of an integer, so truncation gives the exact quotient
     const int seg = (int)(((float)lane + 0.5f) * __frcp_rn((float)g.seg_w));
@@ -222,20 +224,20 @@ __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, in
 
     Words<VW> up = load_row<VW, CHECK>(L, y0 - 1);
     Words<VW> cur = load_row<VW, CHECK>(L, y0);
-    Words<VW> q[kPrefetch];
+    Words<VW> q[PF];
 #pragma unroll
-    for (int i = 0; i < kPrefetch; ++i) q[i] = load_row<VW, CHECK>(L, y0 + 1 + i);
+    for (int i = 0; i < PF; ++i) q[i] = load_row<VW, CHECK>(L, y0 + 1 + i);
     uint32_t up_p = 0, up_n = 0, cur_p, cur_n;
     if constexpr (MODE == MODE_END) side_words<VW>(L, up, up_p, up_n);
     side_words<VW>(L, cur, cur_p, cur_n);
 
 #pragma unroll 1
-    for (int r0 = 0; r0 < RPT; r0 += kPrefetch) {
+    for (int r0 = 0; r0 < RPT; r0 += PF) {
 #pragma unroll
-        for (int j = 0; j < kPrefetch; ++j) {
+        for (int j = 0; j < PF; ++j) {
             const int y = y0 + r0 + j;
             const Words<VW> dn = q[j];
-            if (r0 + j + 1 + kPrefetch <= RPT) q[j] = load_row<VW, CHECK>(L, y + 1 + kPrefetch);
+            if (r0 + j + 1 + PF <= RPT) q[j] = load_row<VW, CHECK>(L, y + 1 + PF);
             uint32_t dn_p, dn_n;
             side_words<VW>(L, dn, dn_p, dn_n);
             if (L.writes && rows_left && (!CHECK || y < g.h))
