@@ -377,24 +377,31 @@ def serve_leg(lib_mod, n_requests=4000, loads=(0.5, 0.9), seed=0):
 def density_leg(lib_mod, stream, reps=64):
     """Section 7: the method's time depends on the image size only.  The
     fused kernel on 4096 x 4096 Bernoulli images of black density 0.1, 0.5
-    and 0.9, rotating 64 buffer pairs (256 MiB) so every launch is cold."""
+    and 0.9, rotating 64 buffer pairs (256 MiB) so every launch is cold.
+    The densities are timed in three interleaved rounds, best round each, so
+    that none of them alone absorbs the clock ramp after the previous leg."""
     import torch
     from paper_1401_5245_gb300 import synth
-    out = {}
-    for p in (0.1, 0.5, 0.9):
+    dens = (0.1, 0.5, 0.9)
+    bufs = {}
+    for p in dens:
         words = synth.pack(synth.bernoulli(4096, 4096, p, 0), 128)
         xs = [torch.from_numpy(words.view(np.int32)).cuda() for _ in range(reps)]
-        ys = [torch.empty_like(xs[0]) for _ in range(reps)]
-        k = [0]
+        bufs[p] = (xs, [torch.empty_like(xs[0]) for _ in range(reps)])
+    best = {p: float("inf") for p in dens}
+    for _ in range(3):
+        for p in dens:
+            xs, ys = bufs[p]
+            k = [0]
 
-        def one():
-            i = k[0] % reps
-            k[0] += 1
-            lib_mod.check(lib_mod.me_edges(xs[i], 4096, 4096, 128, ys[i], 0, stream))
-        one()
-        t = time_events(one, 4 * reps, stream)
-        out[str(p)] = round(t * 1e6, 2)
-        del xs, ys
+            def one():
+                i = k[0] % reps
+                k[0] += 1
+                lib_mod.check(lib_mod.me_edges(xs[i], 4096, 4096, 128, ys[i], 0, stream))
+            one()
+            best[p] = min(best[p], time_events(one, 4 * reps, stream))
+    del bufs
+    out = {str(p): round(best[p] * 1e6, 2) for p in dens}
     vals = list(out.values())
     return {"us_per_image": out, "max_over_min": round(max(vals) / min(vals), 3)}
 
