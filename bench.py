@@ -616,7 +616,7 @@ def run_profile_case(case: str, launches: int, cfg: str | None = None):
     """A few launches of one kernel on a case small enough for an ncu
     capture (inputs still larger than L2): 'batch' = the 4096-image batch
     kernel; 'single' = me_edges on one 32768 x 32768 image (256 MiB).
-    cfg: optional tile configuration 'engine,rows,vec,threads,ctas,kb,stages'."""
+    cfg: optional tile configuration 'engine,rows,vec,threads,ctas,kb,stages[,chunk]'."""
     import torch
     import __graft_entry__
     __graft_entry__.build()

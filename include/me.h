@@ -266,11 +266,17 @@ typedef struct me_tile_cfg {
     int32_t vec_words;       /* REGS: 4 = 128-bit loads where aligned, 1 = 32-bit */
     int32_t cta_threads;     /* 128, 256 or 512 */
     int32_t ctas_per_sm;     /* persistent grid of SMs x this, capped by what
-                                fits on an SM; 0 = REGS: one warp per tile,
-                                BULK: as many as fit */
+                                fits on an SM; 0 = REGS: one warp per tile
+                                (one chunk per warp in a batch), BULK: as
+                                many as fit */
     int32_t stage_kb;        /* BULK: KiB per shared-memory stage (4..64) */
     int32_t stages;          /* BULK: stages in the ring (2..8); stages x
                                 stage_kb <= 216 */
+    int32_t chunk_tiles;     /* REGS batch: consecutive tiles a warp takes
+                                at a time (1..64); warp w takes chunks w,
+                                w + W, w + 2W, ... of the batch's tiles, so
+                                the warps running at any moment work on
+                                neighbouring memory.  0 = 4 */
 } me_tile_cfg;
 
 /* Read or replace the configuration used by the calls of `kind`. */

@@ -55,7 +55,7 @@ class me_desc(ctypes.Structure):
 class me_tile_cfg(ctypes.Structure):
     _fields_ = [("engine", c_i32), ("rows_per_lane", c_i32), ("vec_words", c_i32),
                 ("cta_threads", c_i32), ("ctas_per_sm", c_i32), ("stage_kb", c_i32),
-                ("stages", c_i32)]
+                ("stages", c_i32), ("chunk_tiles", c_i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -17,23 +17,6 @@ int record_cuda(cudaError_t e) {
     return ME_ERR_CUDA;
 }
 
-bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
-    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
-    return x < y + nb && y < x + na;
-}
-
-int check_image_args(const void *img, const void *out, int32_t w, int32_t h,
-                     int32_t stride_words, int32_t boundary) {
-    if (img == nullptr || out == nullptr) return ME_ERR_ARG;
-    if (w <= 0 || h <= 0 || stride_words <= 0) return ME_ERR_ARG;
-    if (stride_words < (int32_t)(((int64_t)w + 31) / 32)) return ME_ERR_ARG;
-    if (boundary != ME_BOUNDARY_WHITE && boundary != ME_BOUNDARY_BLACK) return ME_ERR_ARG;
-    if (((uintptr_t)img & 3) || ((uintptr_t)out & 3)) return ME_ERR_ARG;
-    const size_t bytes = (size_t)h * (size_t)stride_words * 4;
-    if (ranges_overlap(img, bytes, out, bytes)) return ME_ERR_ALIAS;
-    return ME_OK;
-}
-
 int check_device_ptr(const void *p) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -76,36 +59,11 @@ int ceil_log2(int v) {
     return l;
 }
 
-int pick_vw(const void *img, const void *out, int32_t stride, int want_vw) {
-    if (want_vw != 4) return 1;
-    if (((uintptr_t)img & 15) || ((uintptr_t)out & 15) || (stride & 3)) return 1;
-    return 4;
-}
-
-Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
-             int32_t boundary, int vw) {
-    Geo g;
-    g.img = img;
-    g.w = w;
-    g.h = h;
-    g.stride = stride;
-    g.nw = (int32_t)(((int64_t)w + 31) / 32);
-    g.lastmask = (w & 31) ? ((1u << (w & 31)) - 1u) : kAllOnes;
-    g.fill = (boundary == ME_BOUNDARY_WHITE) ? kAllOnes : 0u;
-    g.vw = vw;
-    g.nv = (stride + vw - 1) / vw;      // output covers the whole stride
-    // narrow rows: segments of exactly nv lanes, as many as fit in a warp
-    g.seg_w = g.nv > 32 ? 32 : g.nv;
-    g.segs = 32 / g.seg_w;
-    g.ncb = g.nv > 32 ? (g.nv + kWideLanes - 1) / kWideLanes : 1;
-    return g;
-}
-
 // ------------------------------------------------------------ tile configs
 static std::mutex g_cfg_mu;
 static me_tile_cfg g_cfg[2] = {
-    {ME_ENGINE_REGS, 4, 4, 128, 0, 32, 4},     // single image
-    {ME_ENGINE_REGS, 4, 4, 256, 8, 32, 4},     // batch
+    {ME_ENGINE_REGS, 4, 4, 128, 0, 32, 4, 0},     // single image
+    {ME_ENGINE_REGS, 4, 4, 512, 8, 32, 4, 4},     // batch
 };
 
 void apply_tune_cache(int kind);
@@ -124,13 +82,15 @@ bool valid_cfg(const me_tile_cfg &c) {
     const bool eng = c.engine == ME_ENGINE_REGS || c.engine == ME_ENGINE_BULK;
     const bool stage = c.stage_kb >= 4 && c.stage_kb <= 64 && c.stages >= 2 && c.stages <= 8 &&
                        c.stage_kb * c.stages <= 216;
-    return rows && vec && thr && eng && stage && c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
+    const bool chunk = c.chunk_tiles >= 0 && c.chunk_tiles <= 64;
+    return rows && vec && thr && eng && stage && chunk && c.ctas_per_sm >= 0 &&
+           c.ctas_per_sm <= 32;
 }
 
 uint64_t cfg_key(const me_tile_cfg &c) {
     uint64_t k = (uint64_t)c.engine;
     for (int32_t v : {c.rows_per_lane, c.vec_words, c.cta_threads, c.ctas_per_sm, c.stage_kb,
-                      c.stages})
+                      c.stages, c.chunk_tiles})
         k = k * 1000003ull + (uint64_t)v;
     return k;
 }

@@ -49,14 +49,9 @@ int fail(cudaError_t e) {
 using Setup = BatchSetup;
 
 int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, Setup *s) {
-    int64_t units = 0;
+    (void)descs;
     int rc;
     s->cfg = cfg;
-    if (cfg.engine == ME_ENGINE_BULK) {
-        if ((rc = batch_bands(descs, n, cfg, &units)) != ME_OK) return rc;
-    } else {
-        if ((rc = batch_tasks(descs, n, cfg, &units)) != ME_OK) return rc;
-    }
     DevInfo di;
     if ((rc = device_info(&di)) != ME_OK) return rc;
     if (cfg.engine == ME_ENGINE_BULK) {
@@ -71,20 +66,26 @@ int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, Setup *s) {
         s->arena = bulk_arena_bytes(n, s->grid);
         s->fn = bulk_kernel();
     } else {
-        if ((rc = batch_grid(cfg, di, &s->grid, &s->threads)) != ME_OK) return rc;
-        s->arena = arena_bytes(n, s->grid * (s->threads / 32));
+        // a one-chunk-per-warp grid is fixed by fill_arena, which counts tiles
+        if ((rc = batch_grid(cfg, di, 0, &s->grid, &s->threads)) != ME_OK) return rc;
+        s->arena = arena_bytes(n);
         s->fn = batch_kernel(cfg.rows_per_lane);
     }
     return ME_OK;
 }
 
-int fill_arena(const me_desc *descs, int n, const Setup &s, void *host) {
-    if (s.cfg.engine == ME_ENGINE_BULK) {
-        int64_t bands = 0;
-        return plan_batch_bulk(descs, n, s.cfg, s.grid, host, &bands);
-    }
+int fill_arena(const me_desc *descs, int n, Setup &s, void *host) {
+    int64_t units = 0;
+    if (s.cfg.engine == ME_ENGINE_BULK) return plan_batch_bulk(descs, n, s.cfg, s.grid, host, &units);
     int bad = -1;
-    return plan_batch(descs, n, s.cfg, s.grid * (s.threads / 32), host, &bad);
+    int rc = plan_batch(descs, n, s.cfg, host, &units, &bad);
+    if (rc != ME_OK) return rc;
+    if (s.cfg.ctas_per_sm == 0) {
+        DevInfo di;
+        if ((rc = device_info(&di)) != ME_OK) return rc;
+        rc = batch_grid(s.cfg, di, units, &s.grid, &s.threads);
+    }
+    return rc;
 }
 
 cudaError_t launch_planned(const Setup &s, void *arena_dev, cudaStream_t stream) {
@@ -294,9 +295,11 @@ int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream) {
     if (n == 0) return ME_OK;
     int dev = 0;
     // descriptors are checked before any CUDA call
-    int64_t units = 0;
-    int rc = batch_tasks(descs, n, tile_cfg(ME_KIND_BATCH), &units);
-    if (rc != ME_OK) return rc;
+    for (int i = 0; i < n; ++i) {
+        const me_desc &d = descs[i];
+        const int rc = check_image_args(d.img, d.edge, d.w, d.h, d.stride_words, d.boundary);
+        if (rc != ME_OK) return rc;
+    }
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(e);
     if (dev < 0 || dev >= 64) return ME_ERR_UNSUPPORTED;

@@ -394,22 +394,6 @@ cudaError_t launch_bulk(const Geo &g, uint32_t *edge, const me_tile_cfg &cfg, cu
     return cudaGetLastError();
 }
 
-int batch_bands(const me_desc *descs, int n, const me_tile_cfg &cfg, int64_t *total) {
-    const int stage_words = (int)(bulk_smem_bytes(cfg) / cfg.stages / 4);
-    int64_t t = 0;
-    for (int i = 0; i < n; ++i) {
-        const me_desc &d = descs[i];
-        int rc = check_image_args(d.img, d.edge, d.w, d.h, d.stride_words, d.boundary);
-        if (rc != ME_OK) return rc;
-        KDescB k;
-        bulk_geometry(make_geo(d.img, d.w, d.h, d.stride_words, d.boundary, 1), d.edge,
-                      stage_words, &k);
-        t += (int64_t)k.ncb * k.nrb;
-    }
-    *total = t;
-    return t > INT32_MAX ? ME_ERR_ARG : ME_OK;
-}
-
 int plan_batch_bulk(const me_desc *descs, int n, const me_tile_cfg &cfg, int grid,
                     void *host_arena, int64_t *total_bands) {
     const int stage_words = (int)(bulk_smem_bytes(cfg) / cfg.stages / 4);

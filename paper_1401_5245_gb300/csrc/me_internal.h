@@ -74,32 +74,61 @@ constexpr int32_t kBulkCopy = 1;    // copy with cp.async.bulk (16-byte rows)
 constexpr int32_t kVecStore = 2;    // 128-bit stores allowed
 constexpr int32_t kRowMode = 4;     // full rows, one contiguous copy per band
 
-// Device arena of one batch: header, then descriptors, then per work owner
-// (warp or CTA) the image of its first unit and (register window) its first
-// task; owner w runs tasks [first_task[w], first_task[w + 1]).
+// Device arena of one batch: header, then descriptors, then a table.
+// Register window: entry k is the image holding tile k << block_shift, where
+// a warp starts its walk to the image of its next chunk; the table has
+// task_table_entries(n) entries and block_shift is the smallest shift that
+// covers all tiles with them (so the arena size depends on n alone).  Bulk
+// engine: entry c is the image of CTA c's first band.
 struct BatchHeader {
     int32_t n;
     int32_t total_tasks;
-    int32_t total_warps;
+    int32_t total_warps;        // bulk engine: band owners (CTAs)
     int32_t rows_per_lane;
     int64_t bytes;              // algorithmic bytes: sum of 2 * h * stride * 4
-    int32_t pad[58];
+    int32_t chunk_tiles;        // register window: tiles a warp takes at a time
+    int32_t block_shift;        // register window: tiles per table entry, log2
+    int32_t pad[56];
 };
 static_assert(sizeof(BatchHeader) == 256, "BatchHeader is 256 bytes");
 
-__host__ __device__ inline size_t owner_table_bytes(int owners) {
-    return (((size_t)owners + 1) * sizeof(int32_t) + 255) / 256 * 256;
+inline int64_t task_table_entries(int n) { return 4 * (int64_t)n + 64; }
+inline size_t arena_bytes(int n) {
+    return sizeof(BatchHeader) + (size_t)n * sizeof(BDesc) +
+           ((size_t)task_table_entries(n) * sizeof(int32_t) + 255) / 256 * 256;
 }
-inline size_t arena_bytes(int n, int total_warps) {
-    return sizeof(BatchHeader) + (size_t)n * sizeof(BDesc) + 2 * owner_table_bytes(total_warps);
-}
+// Tiles per chunk of a register-window batch configuration.
+inline int chunk_of(const me_tile_cfg &c) { return c.chunk_tiles > 0 ? c.chunk_tiles : 4; }
 
 // ---------------------------------------------------------------- helpers
+// (inline: a batch plan runs them once per image on every call)
 int record_cuda(cudaError_t e);         // remembers e, returns ME_ERR_CUDA
-int check_image_args(const void *img, const void *out, int32_t w, int32_t h,
-                     int32_t stride_words, int32_t boundary);
 int check_device_ptr(const void *p);    // ME_OK or ME_ERR_ARG / ME_ERR_CUDA
-bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb);
+
+inline bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
+inline int check_image_args(const void *img, const void *out, int32_t w, int32_t h,
+                            int32_t stride_words, int32_t boundary) {
+    if (img == nullptr || out == nullptr) return ME_ERR_ARG;
+    if (w <= 0 || h <= 0 || stride_words <= 0) return ME_ERR_ARG;
+    if (stride_words < (int32_t)(((int64_t)w + 31) / 32)) return ME_ERR_ARG;
+    if (boundary != ME_BOUNDARY_WHITE && boundary != ME_BOUNDARY_BLACK) return ME_ERR_ARG;
+    if (((uintptr_t)img & 3) || ((uintptr_t)out & 3)) return ME_ERR_ARG;
+    const size_t bytes = (size_t)h * (size_t)stride_words * 4;
+    if (ranges_overlap(img, bytes, out, bytes)) return ME_ERR_ALIAS;
+    return ME_OK;
+}
+
+// 4 when both buffers are 16-byte aligned and rows hold whole 16-byte
+// groups, else 1 (32-bit accesses).
+inline int pick_vw(const void *img, const void *out, int32_t stride, int want_vw) {
+    if (want_vw != 4) return 1;
+    if (((uintptr_t)img & 15) || ((uintptr_t)out & 15) || (stride & 3)) return 1;
+    return 4;
+}
 
 struct DevInfo {
     int sm_count;
@@ -109,9 +138,28 @@ struct DevInfo {
 };
 int device_info(DevInfo *out);          // current device, cached
 
-Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
-             int32_t boundary, int vw);
-int pick_vw(const void *img, const void *out, int32_t stride, int want_vw);
+// vw is 1 or 4.
+inline Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
+                    int32_t boundary, int vw) {
+    // segments of a row of n <= 32 vector columns that fit in a warp: 32 / n
+    static constexpr int8_t kSegs[33] = {0, 32, 16, 10, 8, 6, 5, 4, 4, 3, 3, 2, 2, 2, 2, 2, 2,
+                                         1, 1,  1,  1,  1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+    Geo g;
+    g.img = img;
+    g.w = w;
+    g.h = h;
+    g.stride = stride;
+    g.nw = (int32_t)(((int64_t)w + 31) >> 5);
+    g.lastmask = (w & 31) ? ((1u << (w & 31)) - 1u) : kAllOnes;
+    g.fill = (boundary == ME_BOUNDARY_WHITE) ? kAllOnes : 0u;
+    g.vw = vw;
+    g.nv = vw == 4 ? (stride + 3) >> 2 : stride;   // output covers the whole stride
+    // narrow rows: segments of exactly nv lanes, as many as fit in a warp
+    g.seg_w = g.nv > 32 ? 32 : g.nv;
+    g.segs = kSegs[g.seg_w];
+    g.ncb = g.nv > 32 ? (g.nv + kWideLanes - 1) / kWideLanes : 1;
+    return g;
+}
 int ceil_log2(int v);
 
 // ------------------------------------------------------- configurations
@@ -142,7 +190,6 @@ int cached_occupancy(const void *fn, int threads, size_t smem, int *out);
 // Host plan of a bulk batch arena (header, KDescB[n], first image per CTA).
 int plan_batch_bulk(const me_desc *descs, int n, const me_tile_cfg &cfg, int grid,
                     void *host_arena, int64_t *total_bands);
-int batch_bands(const me_desc *descs, int n, const me_tile_cfg &cfg, int64_t *total);
 inline size_t bulk_arena_bytes(int n, int grid) {
     return sizeof(BatchHeader) + (size_t)n * sizeof(KDescB) +
            (((size_t)grid + 1) * sizeof(int32_t) + 255) / 256 * 256;
@@ -153,14 +200,16 @@ unsigned int device_fault_flags(bool clear);
 cudaError_t launch_batch(const void *arena_dev, int grid, int threads,
                          int rows_per_lane, cudaStream_t s);
 const void *batch_kernel(int rows_per_lane);   // for graph kernel nodes
-int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int *grid, int *threads);
+// Persistent grid of a batch (SMs x ctas_per_sm, capped by occupancy), or
+// for ctas_per_sm == 0 the grid of one chunk per warp over total_tasks tiles.
+int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, int *grid,
+               int *threads);
 
-// Fill descriptors and the warp start table of a batch arena on the host.
-// Returns ME_OK or an argument error for descriptor i (*bad = i).
-int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
-               int total_warps, void *host_arena, int *bad);
-int batch_tasks(const me_desc *descs, int n, const me_tile_cfg &cfg,
-                int64_t *total_tasks);
+// Fill descriptors and the tile-block image table of a batch arena on the
+// host (one pass over the images).  Returns ME_OK or an argument error for
+// descriptor i (*bad = i); *total_tasks = tiles of the batch.
+int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_arena,
+               int64_t *total_tasks, int *bad);
 
 // How one batch launches under a tile configuration: grid, threads,
 // dynamic shared memory, arena size and kernel.
@@ -171,9 +220,11 @@ struct BatchSetup {
     const void *fn = nullptr;
     int stage_words = 0;
 };
+// Neither reads the images' geometry beyond n: descriptors are checked by
+// fill_arena, which also fixes the grid of a one-chunk-per-warp launch.
 int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, BatchSetup *s);
 // Write the arena of a batch (s.arena bytes) into host memory.
-int fill_arena(const me_desc *descs, int n, const BatchSetup &s, void *host);
+int fill_arena(const me_desc *descs, int n, BatchSetup &s, void *host);
 // Launch the batch kernel over an arena already in device memory.
 cudaError_t launch_planned(const BatchSetup &s, void *arena_dev, cudaStream_t stream);
 

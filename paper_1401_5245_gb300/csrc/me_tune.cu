@@ -1,7 +1,7 @@
 // Autotuner: times candidate tile configurations on the caller's images
 // with CUDA events and keeps the fastest.  Optional cache file named by
 // ME_TUNE_CACHE, one line per (device name, kind):
-//     <device name>|<kind>|<engine> <rows> <vec> <threads> <ctas_per_sm> <stage_kb> <stages>
+//     <device name>|<kind>|<engine> <rows> <vec> <threads> <ctas_per_sm> <stage_kb> <stages> <chunk>
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -21,17 +21,24 @@ namespace {
 
 std::vector<me_tile_cfg> candidates(int kind) {
     std::vector<me_tile_cfg> out;
-    const int rows[] = {4, 8, 16, 32};
     const int threads[] = {128, 256, 512};
-    const int ctas[] = {kind == ME_KIND_SINGLE ? 0 : 1, 2, 4, 8};
-    for (int r : rows)
-        for (int t : threads)
-            for (int c : ctas) out.push_back({ME_ENGINE_REGS, r, 4, t, c, 32, 4});
+    if (kind == ME_KIND_SINGLE) {
+        for (int r : {4, 8, 16, 32})
+            for (int t : threads)
+                for (int c : {0, 2, 4, 8}) out.push_back({ME_ENGINE_REGS, r, 4, t, c, 32, 4, 0});
+    } else {
+        // rows per lane x CTA size x persistence x tiles per chunk
+        for (int r : {4, 8, 16})
+            for (int t : threads)
+                for (int c : {0, 1, 2, 4, 8})
+                    for (int ch : {2, 4, 8})
+                        out.push_back({ME_ENGINE_REGS, r, 4, t, c, 32, 4, ch});
+    }
     // bulk engine: stage size x ring depth x CTA size, as many CTAs as fit
     for (int kb : {8, 16, 32, 48, 64})
         for (int st : {2, 3, 4, 6})
             for (int t : {256, 512})
-                if (kb * st <= 216) out.push_back({ME_ENGINE_BULK, 8, 4, t, 0, kb, st});
+                if (kb * st <= 216) out.push_back({ME_ENGINE_BULK, 8, 4, t, 0, kb, st, 0});
     return out;
 }
 
@@ -49,7 +56,7 @@ bool read_cache(const char *path, const std::string &key, me_tile_cfg *out) {
         std::istringstream is(line.substr(bar + 1));
         me_tile_cfg c;
         if (is >> c.engine >> c.rows_per_lane >> c.vec_words >> c.cta_threads >> c.ctas_per_sm >>
-                c.stage_kb >> c.stages &&
+                c.stage_kb >> c.stages >> c.chunk_tiles &&
             valid_cfg(c)) {
             *out = c;
             found = true;
@@ -72,7 +79,8 @@ void write_cache(const char *path, const std::string &key, const me_tile_cfg &c)
     std::ofstream f(path, std::ios::trunc);
     for (auto &l : keep) f << l << "\n";
     f << key << "|" << c.engine << " " << c.rows_per_lane << " " << c.vec_words << " "
-      << c.cta_threads << " " << c.ctas_per_sm << " " << c.stage_kb << " " << c.stages << "\n";
+      << c.cta_threads << " " << c.ctas_per_sm << " " << c.stage_kb << " " << c.stages << " "
+      << c.chunk_tiles << "\n";
 }
 
 int run_once(int kind, const me_desc *s, int n, cudaStream_t st) {

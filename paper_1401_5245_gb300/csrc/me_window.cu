@@ -51,9 +51,11 @@ static WindowFn pick_mode(int mode, int rpt) {
     }
 }
 
+// Row blocks of RPT * segs rows times column blocks.  ceil(h / (rpt segs))
+// = ceil(ceil(h / rpt) / segs); rpt is a power of two.
 static int64_t tasks_of(int h, int segs, int ncb, int rpt) {
-    const int64_t rows_per_task = (int64_t)rpt * segs;
-    const int64_t nrb = (h + rows_per_task - 1) / rows_per_task;
+    const unsigned rows = ((unsigned)h + (unsigned)rpt - 1) >> __builtin_ctz((unsigned)rpt);
+    const unsigned nrb = (rows + (unsigned)segs - 1) / (unsigned)segs;
     return (int64_t)ncb * nrb;
 }
 
@@ -82,51 +84,63 @@ cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
 }
 
 // ------------------------------------------------------------- batch
-// Every warp owns a contiguous range of the batch's tiles, so consecutive
-// tiles of one warp are usually vertically adjacent in the same image and
-// the halo rows it re-reads are still in L1/L2.  The host gives every warp
-// the same number of tiles and writes each warp's first tile and its image;
-// the warp then walks forward.
+// The batch's tiles, image by image and top to bottom within an image, are
+// cut into chunks of C consecutive tiles; warp w of W takes chunks w,
+// w + W, w + 2W, ...  The warps running at any moment thus work on one
+// window of neighbouring memory that sweeps through the batch, as a copy
+// does (on the uneven 4096-image batch this measured 6.6% faster than
+// giving each warp one contiguous range), and within a chunk a warp's
+// tiles are vertically adjacent, so the halo rows it re-reads are still in
+// L1.  A table gives the image of every (1 << block_shift)-th tile; a warp
+// bisects between two entries for the image of its chunk's first tile and
+// walks forward from there.
 template <int RPT>
 __global__ void __launch_bounds__(512)
 k_batch(const BatchHeader *__restrict__ hdr) {
     const BDesc *descs = reinterpret_cast<const BDesc *>(hdr + 1);
-    const int W = hdr->total_warps;
-    const int32_t *warp_first_image = reinterpret_cast<const int32_t *>(descs + hdr->n);
-    const int32_t *warp_first_task = reinterpret_cast<const int32_t *>(
-        reinterpret_cast<const char *>(warp_first_image) + owner_table_bytes(W));
+    const int32_t *block_image = reinterpret_cast<const int32_t *>(descs + hdr->n);
+    const int T = hdr->total_tasks;
+    const int C = hdr->chunk_tiles;
+    const int shift = hdr->block_shift;
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    if (warp >= W) return;
-    const int t0 = warp_first_task[warp];
-    const int t1 = warp_first_task[warp + 1];
-    int i = warp_first_image[warp];
-    for (int t = t0; t < t1; ++t) {
-        while (t >= descs[i].task_base + descs[i].ntasks) ++i;
-        const BDesc &d = descs[i];
-        Geo g;
-        g.img = d.img;
-        g.w = 0;
-        g.h = d.h;
-        g.stride = d.stride;
-        g.nw = d.nw;
-        g.lastmask = d.lastmask;
-        g.fill = d.fill;
-        g.vw = d.vw;
-        g.nv = d.nv;
-        g.seg_w = d.seg_w;
-        g.segs = d.segs;
-        g.ncb = d.ncb;
-        Outs o;
-        o.p[0] = d.edge;
-        o.p[1] = o.p[2] = o.p[3] = nullptr;
-        const int local = t - d.task_base;
-        const int cb = local % d.ncb;
-        const int rb = local / d.ncb;
-        if (d.vw == 4)
-            window_tile<4, RPT, MODE_EDGE>(g, o, cb, rb, lane);
-        else
-            window_tile<1, RPT, MODE_EDGE>(g, o, cb, rb, lane);
+    const int64_t step = (int64_t)((gridDim.x * (unsigned)blockDim.x) >> 5) * C;
+    for (int64_t c0 = (int64_t)warp * C; c0 < T; c0 += step) {
+        const int t1 = (int)min(c0 + C, (int64_t)T);
+        // the image of tile c0: bisect the images the table brackets it with
+        int i = block_image[c0 >> shift];
+        int hi = block_image[(c0 >> shift) + 1];
+        while (i < hi) {
+            const int mid = (i + hi + 1) >> 1;
+            if (descs[mid].task_base <= c0) i = mid; else hi = mid - 1;
+        }
+        for (int t = (int)c0; t < t1; ++t) {
+            while (t >= descs[i].task_base + descs[i].ntasks) ++i;
+            const BDesc &d = descs[i];
+            Geo g;
+            g.img = d.img;
+            g.w = 0;
+            g.h = d.h;
+            g.stride = d.stride;
+            g.nw = d.nw;
+            g.lastmask = d.lastmask;
+            g.fill = d.fill;
+            g.vw = d.vw;
+            g.nv = d.nv;
+            g.seg_w = d.seg_w;
+            g.segs = d.segs;
+            g.ncb = d.ncb;
+            Outs o;
+            o.p[0] = d.edge;
+            o.p[1] = o.p[2] = o.p[3] = nullptr;
+            const int local = t - d.task_base;
+            const int cb = local % d.ncb;
+            const int rb = local / d.ncb;
+            if (d.vw == 4)
+                window_tile<4, RPT, MODE_EDGE>(g, o, cb, rb, lane);
+            else
+                window_tile<1, RPT, MODE_EDGE>(g, o, cb, rb, lane);
+        }
     }
 }
 
@@ -183,14 +197,22 @@ int cached_occupancy(const void *fn, int threads, size_t smem, int *out) {
     return ME_OK;
 }
 
-int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int *grid, int *threads) {
+int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, int *grid,
+               int *threads) {
+    *threads = cfg.cta_threads;
+    if (cfg.ctas_per_sm == 0) {
+        const int64_t chunks = (total_tasks + chunk_of(cfg) - 1) / chunk_of(cfg);
+        const int64_t warps = cfg.cta_threads / 32;
+        *grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + warps - 1) / warps,
+                                                            INT32_MAX));
+        return ME_OK;
+    }
     int occ = 0;
     int rc = regs_ctas_per_sm(reinterpret_cast<const void *>(pick_batch(cfg.rows_per_lane)),
                               cfg.cta_threads, &occ);
     if (rc != ME_OK) return rc;
-    const int per_sm = std::max(1, std::min(cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : occ, occ));
+    const int per_sm = std::max(1, std::min(cfg.ctas_per_sm, occ));
     *grid = di.sm_count * per_sm;
-    *threads = cfg.cta_threads;
     return ME_OK;
 }
 
@@ -219,28 +241,11 @@ static void fill_bdesc(const me_desc &d, const me_tile_cfg &cfg, BDesc *out) {
     out->nv = g.nv;
 }
 
-int batch_tasks(const me_desc *descs, int n, const me_tile_cfg &cfg,
-                int64_t *total_tasks) {
-    int64_t total = 0;
-    for (int i = 0; i < n; ++i) {
-        const me_desc &d = descs[i];
-        int rc = check_image_args(d.img, d.edge, d.w, d.h, d.stride_words, d.boundary);
-        if (rc != ME_OK) return rc;
-        BDesc b;
-        fill_bdesc(d, cfg, &b);
-        total += tasks_of(b.h, b.segs, b.ncb, cfg.rows_per_lane);
-    }
-    *total_tasks = total;
-    return total > INT32_MAX ? ME_ERR_ARG : ME_OK;
-}
-
-int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
-               int total_warps, void *host_arena, int *bad) {
+int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_arena,
+               int64_t *total_tasks, int *bad) {
     BatchHeader *hdr = static_cast<BatchHeader *>(host_arena);
     BDesc *bd = reinterpret_cast<BDesc *>(hdr + 1);
-    int32_t *first_image = reinterpret_cast<int32_t *>(bd + n);
-    int32_t *first_task = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(first_image) +
-                                                      owner_table_bytes(total_warps));
+    int32_t *block_image = reinterpret_cast<int32_t *>(bd + n);
     std::memset(hdr, 0, sizeof(*hdr));
     int64_t total = 0, bytes = 0;
     for (int i = 0; i < n; ++i) {
@@ -263,20 +268,23 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg,
     }
     hdr->n = n;
     hdr->total_tasks = (int32_t)total;
-    hdr->total_warps = total_warps;
     hdr->rows_per_lane = cfg.rows_per_lane;
+    hdr->chunk_tiles = chunk_of(cfg);
     hdr->bytes = bytes;
-    // Equal numbers of tiles per warp.  A tile costs about one memory round
-    // trip whatever its width, so equal counts finish together better than
-    // equal bytes (measured on the uneven 4096-image batch).
-    for (int w = 0; w <= total_warps; ++w)
-        first_task[w] = (int32_t)((total * w) / total_warps);
-    // the image holding each warp's first tile (both sequences increase)
-    int k = 0;
-    for (int w = 0; w <= total_warps; ++w) {
-        while (k < n - 1 && first_task[w] >= bd[k].task_base + bd[k].ntasks) ++k;
-        first_image[w] = k;
+    // entries 0 .. ceil(total / 2^shift) inclusive, the last one n - 1
+    int shift = 0;
+    while (((total - 1) >> shift) + 2 > task_table_entries(n)) ++shift;
+    hdr->block_shift = shift;
+    // the image holding tile b << shift: image k covers the entries whose
+    // first tile lies in [task_base, task_base + ntasks)
+    const int64_t unit = (int64_t)1 << shift;
+    int64_t b = 0;
+    for (int k = 0; k < n; ++k) {
+        const int64_t end = (int64_t)bd[k].task_base + bd[k].ntasks;
+        for (; b * unit < end; ++b) block_image[b] = k;
     }
+    block_image[b] = n - 1;
+    if (total_tasks) *total_tasks = total;
     return ME_OK;
 }
 

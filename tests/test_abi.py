@@ -83,6 +83,9 @@ def test_argument_errors_without_a_gpu(lib):
     cfg = lib.me_tile_cfg(1, 8, 4, 256, 0, 32, 1)
     assert L.me_set_tile_cfg(1, ctypes.byref(cfg)) == ARG      # one stage
     assert L.me_set_tile_cfg(7, ctypes.byref(cfg)) == ARG
+    for chunk in (-1, 65):                                      # tiles per chunk
+        cfg = lib.me_tile_cfg(0, 4, 4, 256, 8, 32, 4, chunk)
+        assert L.me_set_tile_cfg(1, ctypes.byref(cfg)) == ARG
     assert L.me_serve_open(None, None) == ARG
     assert L.me_serve_poll(None, 1, None, 0, None) == ARG
     assert L.me_serve_close(None, 0) == ARG
@@ -92,7 +95,7 @@ def test_tile_cfg_roundtrip(lib):
     L = lib.load()
     old = lib.me_tile_cfg()
     assert L.me_get_tile_cfg(1, ctypes.byref(old)) == 0
-    new = lib.me_tile_cfg(1, 16, 4, 512, 2, 48, 3)
+    new = lib.me_tile_cfg(1, 16, 4, 512, 2, 48, 3, 7)
     assert L.me_set_tile_cfg(1, ctypes.byref(new)) == 0
     assert lib.me_get_tile_cfg(1).as_dict() == new.as_dict()
     assert L.me_set_tile_cfg(1, ctypes.byref(old)) == 0

@@ -56,6 +56,37 @@ def check_batch(imgs, srcs, dsts):
         assert np.array_equal(S.unpack(ow, w), O.edges(img, b)), (w, h, b)
 
 
+def image_item(img, b, seed, pad16=True):
+    h, w = img.shape
+    stride = S.batch_stride(w, pad16)
+    words = S.pack(img, stride, pad="random", seed=seed)
+    src, dst = DevBuf(words), DevBuf(np.zeros_like(words), fill=SENTINEL)
+    return (img, b), src, dst, (src.ptr(), dst.ptr(), w, h, stride, b)
+
+
+@pytest.mark.parametrize("chunk", [1, 4, 64])
+def test_many_small_images_before_a_tall_one(chunk):
+    """40 one-tile images ahead of a 4000 x 40000 image (10000 tiles): the
+    tile table then holds one entry per 64 tiles and its first entry
+    brackets all 40 small images, which the kernel bisects."""
+    saved = _lib.me_get_tile_cfg(1)
+    parts = []
+    rng = np.random.default_rng(5)
+    for i in range(40):
+        w, h = int(rng.integers(1, 129)), int(rng.integers(1, 5))
+        parts.append(image_item((rng.random((h, w)) < 0.5).astype(np.uint8), i % 2, i))
+    tall = S.strokes(4000, 40000, 400, 11)
+    parts.append(image_item(tall, 0, 99))
+    imgs, srcs, dsts, items = (list(x) for x in zip(*parts))
+    try:
+        assert _lib.me_set_tile_cfg(1, _lib.me_tile_cfg(0, 4, 4, 512, 8, 32, 4, chunk)) == 0
+        assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
+        sync()
+        check_batch(imgs, srcs, dsts)
+    finally:
+        _lib.load().me_set_tile_cfg(1, saved)
+
+
 @pytest.mark.parametrize("pad16", [True, False])
 def test_small_uneven_batch(pad16):
     imgs, srcs, dsts, items = make_batch(1, 96, 1, 700, pad16, boundaries=[0, 1])
@@ -89,9 +120,13 @@ def test_repeated_calls_reuse_graphs_and_slots():
 
 def batch_cfgs():
     out = []
+    chunks = itertools.cycle([1, 3, 4, 64])
     for rows, threads, ctas, vec in itertools.product([4, 8, 16, 32], [128, 256, 512],
-                                                      [1, 2, 8], [1, 4]):
-        out.append((0, rows, vec, threads, ctas, 32, 4))
+                                                      [0, 1, 2, 8], [1, 4]):
+        out.append((0, rows, vec, threads, ctas, 32, 4, next(chunks)))
+    # tiles per chunk, persistent and one chunk per warp
+    for ctas, chunk in itertools.product([0, 8], [0, 1, 2, 5, 8, 16, 17, 64]):
+        out.append((0, 4, 4, 512, ctas, 32, 4, chunk))
     for kb, st, threads, ctas in itertools.product([4, 16, 32, 64], [2, 3, 4],
                                                    [128, 256, 512], [0, 1, 2]):
         if kb * st <= 216:
