@@ -272,6 +272,29 @@ def test_host_batch_gaps_unaligned_and_pinned():
     assert _lib.me_device_faults(clear=True) == 0
 
 
+def at_page_offset(a, offset):
+    """A copy of `a` whose first byte sits `offset` bytes past a 4 KiB page."""
+    raw = np.empty(a.size + 2048, dtype=np.uint32)
+    skip = ((offset - raw.ctypes.data) % 4096) // 4
+    out = raw[skip:skip + a.size]
+    out[:] = a
+    assert out.ctypes.data % 4096 == offset
+    return out
+
+
+@pytest.mark.parametrize("in_off,out_off", [(48, 2064), (4080, 16), (4, 4092)])
+def test_host_batch_page_offsets(in_off, out_off):
+    """Copies are split at host page boundaries and the first chunk's upload
+    cannot start below the input buffer: buffers that start part way into a
+    page, small chunks so most chunks start mid-page, gaps between images."""
+    imgs, items, buf = host_batch(23, 80, 1, 700, gap_words=3, align4=in_off % 16 == 0)
+    src = at_page_offset(buf, in_off)
+    out = at_page_offset(np.full_like(buf, SENTINEL), out_off)
+    rc = _lib.me_edges_batch_host(src, out, _lib.make_host_images(items), len(items), 64 << 10)
+    assert rc == 0, _lib.status_string(rc)
+    check_host(imgs, items, out)
+
+
 def test_host_batch_errors():
     imgs, items, buf = host_batch(22, 4, 16, 64)
     L = _lib.load()
