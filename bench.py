@@ -296,7 +296,76 @@ def time_events(fn, reps, stream):
     return a.elapsed_time(b) / 1e3 / reps
 
 
-def serve_leg(lib_mod, n_requests=4000, loads=(0.5, 0.9), seed=0):
+def median_events(fn, reps, stream):
+    """Median of `reps` launches, each timed alone with its own event pair."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs) / 1e3
+
+
+def c1_leg(lib_mod, stream, seeds=(0, 1, 2), reps=2000):
+    """256 x 256 glyph pages (8 KiB packed): launch-bound.  Device time per
+    call back to back, and the host round trip of one call (call + stream
+    synchronize), median; every result checked against the oracle."""
+    import torch
+    from oracle import oracle
+    from paper_1401_5245_gb300 import synth
+    out, exact = {}, True
+    for seed in seeds:
+        img = synth.ellipse_glyphs(seed)
+        words = synth.pack(img, 8)
+        x = torch.from_numpy(words.view(np.int32)).cuda()
+        y = torch.empty_like(x)
+
+        def one():
+            lib_mod.check(lib_mod.me_edges(x, 256, 256, 8, y, 0, stream))
+        one()
+        torch.cuda.synchronize()
+        exact &= bool(np.array_equal(synth.unpack(y.cpu().numpy().view(np.uint32), 256),
+                                     oracle.edges(img, 0)))
+        t_dev = time_events(one, reps, stream)
+        rt = []
+        for _ in range(200):
+            t0 = time.perf_counter()
+            one()
+            stream.synchronize()
+            rt.append(time.perf_counter() - t0)
+        out[str(seed)] = {"us_per_call_back_to_back": round(t_dev * 1e6, 2),
+                          "host_round_trip_us_p50": round(statistics.median(rt) * 1e6, 1)}
+    return {"per_seed": out, "exact": exact,
+            "gpixel_s_back_to_back": round(65536 / statistics.mean(
+                v["us_per_call_back_to_back"] for v in out.values()) / 1e3, 2)}
+
+
+def unpadded_leg(lib_mod, stream, peak):
+    """The uneven batch with stride = ceil(w / 32) (no padding to 16 bytes):
+    rows are not 16-byte groups, so every image takes the 32-bit path."""
+    import torch
+    from paper_1401_5245_gb300 import synth
+    batch = synth.batch(0, N_IMAGES, pad16=False, workers=min(16, os.cpu_count() or 1))
+    dev_in, dev_out, _, _, offs = upload_batch(batch, torch.device("cuda", 0))
+    descs = descs_for(lib_mod, batch, dev_in, dev_out, offs)
+    plan = lib_mod.BatchPlan(descs, len(batch), stream)
+    lib_mod.check(plan.run(stream))
+    torch.cuda.synchronize()
+    exact, n = verify_sample(batch, dev_out, offs)
+    t = time_events(lambda: plan.run(stream), 200, stream)
+    nbytes = plan.bytes
+    plan.close()
+    px = sum(im.pixels for im in batch)
+    return {"gpixel_s": round(px / t / 1e9, 1), "gb_s": round(nbytes / t / 1e9, 1),
+            "frac_of_peak": round(nbytes / t / 1e9 / peak, 4), "us": round(t * 1e6, 1),
+            "exact": exact, "exact_images_checked": n}
+
+
+def serve_leg(lib_mod, n_requests=20000, loads=(0.25, 0.5, 0.8, 0.95), seed=0):
     """Serving: requests drawn from the 48x48 / 1024x1024 / 2480x3508 mix
     (70/25/5 %), an 8 GiB device budget.  First the closed-loop saturated
     rate (everything submitted at once), then Poisson arrivals at fractions
@@ -347,7 +416,8 @@ def serve_leg(lib_mod, n_requests=4000, loads=(0.5, 0.9), seed=0):
         result["saturated"] = {"req_per_s": round(sat_rate, 1),
                                "gpixel_s": round(px / wall / 1e9, 3),
                                "p50_us": round(float(np.percentile(lat, 50)), 1),
-                               "p99_us": round(float(np.percentile(lat, 99)), 1)}
+                               "p99_us": round(float(np.percentile(lat, 99)), 1),
+                               "max_us": round(float(lat.max()), 1)}
         for f in loads:
             t_arr, _ = synth.serve_trace(seed + 7, n_requests, f * sat_rate)
             wall, lat = run(t_arr)
@@ -400,10 +470,28 @@ def density_leg(lib_mod, stream, reps=64):
                 lib_mod.check(lib_mod.me_edges(xs[i], 4096, 4096, 128, ys[i], 0, stream))
             one()
             best[p] = min(best[p], time_events(one, 4 * reps, stream))
-    del bufs
+    # the same image again and again (2 MiB in + out stay in L2), and the
+    # staged five-pass form HBM-cold
+    xs, ys = bufs[0.5]
+    lib_mod.check(lib_mod.me_edges(xs[0], 4096, 4096, 128, ys[0], 0, stream))
+    t_l2 = time_events(lambda: lib_mod.check(
+        lib_mod.me_edges(xs[0], 4096, 4096, 128, ys[0], 0, stream)), 4 * reps, stream)
+    k = [0]
+
+    def staged():
+        i = k[0] % reps
+        k[0] += 1
+        lib_mod.check(lib_mod.me_edges_staged(xs[i], 4096, 4096, 128, ys[i], 0, stream))
+    staged()
+    t_staged = time_events(staged, reps, stream)
+    del bufs, xs, ys
     out = {str(p): round(best[p] * 1e6, 2) for p in dens}
     vals = list(out.values())
-    return {"us_per_image": out, "max_over_min": round(max(vals) / min(vals), 3)}
+    return {"us_per_image": out, "max_over_min": round(max(vals) / min(vals), 3),
+            "l2_resident_us": round(t_l2 * 1e6, 2),
+            "staged_hbm_cold_us": round(t_staged * 1e6, 2),
+            "gpixel_s_hbm_cold": round(4096 * 4096 / best[0.5] / 1e9, 1),
+            "gpixel_s_l2_resident": round(4096 * 4096 / t_l2 / 1e9, 1)}
 
 
 def cpu_baseline_leg(batch, budget_s=20.0):
@@ -423,6 +511,47 @@ def cpu_baseline_leg(batch, budget_s=20.0):
     return {"value": px / t_used / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} of the {len(batch)} batch images ({px / 1e9:.3f} Gpixel), "
                       f"single-threaded C oracle, unpack not timed"}
+
+
+def _oracle_proc(images, barrier, queue):
+    """One worker of the all-cores CPU baseline: unpack its images, wait for
+    the others, then run the oracle on them."""
+    from oracle import oracle
+    from paper_1401_5245_gb300 import synth
+    oracle.build()
+    t = time.perf_counter()
+    unpacked = [synth.unpack(words, w) for words, w in images]
+    t_unpack = time.perf_counter() - t
+    barrier.wait()
+    t0 = time.time()
+    px = 0
+    for img in unpacked:
+        oracle.edges(img, 0)
+        px += img.size
+    queue.put((t0, time.time(), t_unpack, px))
+
+
+def cpu_all_cores_leg(batch):
+    """The oracle on every host core at once (one spawned process per core,
+    images dealt round-robin, started together); unpacking is done before
+    the start and reported on its own."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    n = os.cpu_count() or 1
+    barrier, queue = ctx.Barrier(n), ctx.Queue()
+    order = sorted(range(len(batch)), key=lambda i: -batch[i].pixels)
+    parts = [[(batch[i].words, batch[i].w) for i in order[k::n]] for k in range(n)]
+    procs = [ctx.Process(target=_oracle_proc, args=(parts[k], barrier, queue)) for k in range(n)]
+    for p in procs:
+        p.start()
+    res = [queue.get(timeout=600) for _ in procs]
+    for p in procs:
+        p.join()
+    wall = max(r[1] for r in res) - min(r[0] for r in res)
+    px = sum(r[3] for r in res)
+    return {"value": round(px / wall / 1e9, 3), "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"all {len(batch)} batch images ({px / 1e9:.3f} Gpixel), {n} processes",
+            "unpack_s_per_gpixel_one_core": round(sum(r[2] for r in res) / (px / 1e9), 3)}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -564,6 +693,7 @@ def run_ours(args, rank, world, local_rank):
                          stream=stream)
         single()
         t_single = time_events(single, 60, stream)
+        t_single_med = median_events(single, 60, stream)
         b1 = 2 * h * 1024 * 4
         def staged1():
             i = k[0] % 3
@@ -578,13 +708,16 @@ def run_ours(args, rank, world, local_rank):
                                 "gb_s": round(b1 / t_single / 1e9, 1),
                                 "frac_of_peak": round(b1 / t_single / 1e9 / peak, 4),
                                 "us": round(t_single * 1e6, 2),
+                                "us_median_of_60_single_launches": round(t_single_med * 1e6, 2),
                                 "tile_cfg": _lib.me_get_tile_cfg(0).as_dict()}
         extra["staged_32768"] = {"gpixel_s": round(w * h / t_staged1 / 1e9, 1),
                                  "us": round(t_staged1 * 1e6, 2)}
         del xs, ys
 
     if not args.quick:
+        extra["c1_256"] = c1_leg(_lib, stream)
         extra["data_independence_4096"] = density_leg(_lib, stream)
+        extra["unpadded_batch"] = unpadded_leg(_lib, stream, peak)
         extra["serve"] = serve_leg(_lib)
 
     cfg = _lib.me_get_tile_cfg(1).as_dict()
@@ -605,6 +738,8 @@ def run_ours(args, rank, world, local_rank):
            "e2e": e2e, "roofline": roofline, "clocks": clocks, "extra": extra}
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline_leg(batch, budget_s=args.cpu_budget)
+        if not args.quick:
+            extra["cpu_all_cores"] = cpu_all_cores_leg(batch)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
