@@ -263,7 +263,12 @@ int me_edges_batch_host(const uint32_t *host_in, uint32_t *host_out,
 typedef struct me_tile_cfg {
     int32_t engine;          /* ME_ENGINE_REGS or ME_ENGINE_BULK */
     int32_t rows_per_lane;   /* REGS: rows one lane walks: 4, 8, 16 or 32 */
-    int32_t vec_words;       /* REGS: 4 = 128-bit loads where aligned, 1 = 32-bit */
+    int32_t vec_words;       /* REGS: 4 = four words per lane, moved as one
+                                128-bit access where both buffers are 16-byte
+                                aligned and stride_words % 4 == 0, else as
+                                four 32-bit accesses; 1 = 32-bit accesses only
+                                (single images: one word per lane; batches:
+                                four words per lane) */
     int32_t cta_threads;     /* 128, 256 or 512 */
     int32_t ctas_per_sm;     /* persistent grid of SMs x this, capped by what
                                 fits on an SM; 0 = REGS: one warp per tile
@@ -374,10 +379,13 @@ int me_serve_stats(me_server *srv, int64_t *submitted, int64_t *completed,
 int me_serve_close(me_server *srv, int64_t drain_timeout_us);
 
 /*
- * Bounded waits that ran out in library kernels since the last clear, as
- * a bit set (0 in a healthy run; bit 0: a bulk-copy stage never arrived, the
- * kernel stopped early and its outputs are incomplete).  clear != 0 resets
- * it.  Synchronises with the current device.
+ * Faults that library kernels recorded since the last clear, as a bit set
+ * (0 in a healthy run).  Bit 0: a bounded wait ran out (a bulk-copy stage
+ * never arrived); the kernel stopped early and its outputs are incomplete.
+ * Bit 1: the batch kernel without 32-bit tiles met an image that needs them
+ * and skipped its tiles (the library picks the kernel from the same test,
+ * so this marks a library fault).  clear != 0 resets both.  Synchronises
+ * with the current device.
  */
 int me_device_faults(int32_t clear, uint32_t *flags);
 

@@ -132,7 +132,7 @@ int me_device_faults(int32_t clear, uint32_t *flags) {
     if (flags == nullptr) return ME_ERR_ARG;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return record_cuda(e);
-    *flags = device_fault_flags(clear != 0);
+    *flags = device_fault_flags(clear != 0) | window_fault_flags(clear != 0);
     return ME_OK;
 }
 
@@ -160,8 +160,8 @@ static int single_call(int mode, const uint32_t *img, int32_t w, int32_t h,
     if ((rc = check_device_ptr(img)) != ME_OK) return rc;
     if ((rc = check_device_ptr(out)) != ME_OK) return rc;
     const me_tile_cfg cfg = tile_cfg(ME_KIND_SINGLE);
-    const Geo g = make_geo(img, w, h, stride_words, boundary,
-                           pick_vw(img, out, stride_words, cfg.vec_words));
+    const Geo g = make_geo(img, w, h, stride_words, boundary, pick_vw(cfg.vec_words),
+                           vec16_ok(img, out, stride_words));
     cudaError_t e;
     if (mode == MODE_EDGE && cfg.engine == ME_ENGINE_BULK) {
         e = launch_bulk(g, out, cfg, (cudaStream_t)stream);
@@ -206,9 +206,9 @@ int me_fundamental_edges(const uint32_t *img, int32_t w, int32_t h,
     for (int k = 0; k < 4; ++k)
         if ((rc = check_device_ptr(outs[k])) != ME_OK) return rc;
     const me_tile_cfg cfg = tile_cfg(ME_KIND_SINGLE);
-    int vw = 4;
-    for (int k = 0; k < 4; ++k) vw = std::min(vw, pick_vw(img, outs[k], stride_words, cfg.vec_words));
-    const Geo g = make_geo(img, w, h, stride_words, boundary, vw);
+    bool vec16 = true;
+    for (int k = 0; k < 4; ++k) vec16 = vec16 && vec16_ok(img, outs[k], stride_words);
+    const Geo g = make_geo(img, w, h, stride_words, boundary, pick_vw(cfg.vec_words), vec16);
     Outs o = {{left, right, up, down}};
     cudaError_t e = launch_window(MODE_FUND, g, o, cfg, (cudaStream_t)stream);
     return e == cudaSuccess ? ME_OK : record_cuda(e);

@@ -67,9 +67,9 @@ int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, Setup *s) {
         s->fn = bulk_kernel();
     } else {
         // a one-chunk-per-warp grid is fixed by fill_arena, which counts tiles
-        if ((rc = batch_grid(cfg, di, 0, &s->grid, &s->threads)) != ME_OK) return rc;
+        if ((rc = batch_grid(cfg, di, 0, false, &s->grid, &s->threads)) != ME_OK) return rc;
         s->arena = arena_bytes(n);
-        s->fn = batch_kernel(cfg.rows_per_lane);
+        s->fn = batch_kernel(cfg.rows_per_lane, false);
     }
     return ME_OK;
 }
@@ -78,12 +78,15 @@ int fill_arena(const me_desc *descs, int n, Setup &s, void *host) {
     int64_t units = 0;
     if (s.cfg.engine == ME_ENGINE_BULK) return plan_batch_bulk(descs, n, s.cfg, s.grid, host, &units);
     int bad = -1;
-    int rc = plan_batch(descs, n, s.cfg, host, &units, &bad);
+    bool any = false;
+    int rc = plan_batch(descs, n, s.cfg, host, &units, &any, &bad);
     if (rc != ME_OK) return rc;
-    if (s.cfg.ctas_per_sm == 0) {
+    s.any = any;
+    s.fn = batch_kernel(s.cfg.rows_per_lane, any);
+    if (any || s.cfg.ctas_per_sm == 0) {
         DevInfo di;
         if ((rc = device_info(&di)) != ME_OK) return rc;
-        rc = batch_grid(s.cfg, di, units, &s.grid, &s.threads);
+        rc = batch_grid(s.cfg, di, units, any, &s.grid, &s.threads);
     }
     return rc;
 }
@@ -227,7 +230,7 @@ int BatchRing::launch(const me_desc *descs, int n, cudaStream_t stream) {
         copy_ = nullptr;
         return fail(e);
     }
-    const uint64_t key = cfg_key(su.cfg) * 31 + (uint64_t)su.grid;
+    const uint64_t key = (cfg_key(su.cfg) * 31 + (uint64_t)su.grid) * 2 + (su.any ? 1 : 0);
     auto it = slot.graphs.find(key);
     if (it == slot.graphs.end()) {
         GraphEntry ge;

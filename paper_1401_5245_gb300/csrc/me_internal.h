@@ -33,6 +33,7 @@ struct Geo {
     uint32_t lastmask;          // valid bits of word nw - 1
     uint32_t fill;              // outside colour as a word: ~0 white, 0 black
     int32_t vw;                 // words per lane and row: 4 or 1
+    int32_t vec16;              // vw == 4: the 4 words move as one 128-bit access
     int32_t nv;                 // vector columns written: ceil(stride / vw)
     int32_t seg_w;              // lanes one row segment uses (nv, or 32 when wide)
     int32_t segs;               // row segments stacked in one warp (32 / seg_w)
@@ -122,12 +123,12 @@ inline int check_image_args(const void *img, const void *out, int32_t w, int32_t
     return ME_OK;
 }
 
-// 4 when both buffers are 16-byte aligned and rows hold whole 16-byte
-// groups, else 1 (32-bit accesses).
-inline int pick_vw(const void *img, const void *out, int32_t stride, int want_vw) {
-    if (want_vw != 4) return 1;
-    if (((uintptr_t)img & 15) || ((uintptr_t)out & 15) || (stride & 3)) return 1;
-    return 4;
+// Words per lane and row: 4 unless the configuration asks for 1.
+inline int pick_vw(int want_vw) { return want_vw == 4 ? 4 : 1; }
+// A lane's 4 words move as one 128-bit access when both buffers are 16-byte
+// aligned and rows hold whole 16-byte groups, else as four 32-bit accesses.
+inline bool vec16_ok(const void *img, const void *out, int32_t stride) {
+    return !(((uintptr_t)img & 15) || ((uintptr_t)out & 15) || (stride & 3));
 }
 
 struct DevInfo {
@@ -138,9 +139,9 @@ struct DevInfo {
 };
 int device_info(DevInfo *out);          // current device, cached
 
-// vw is 1 or 4.
+// vw is 1 or 4; vec16 (vw == 4 only): 128-bit accesses allowed.
 inline Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
-                    int32_t boundary, int vw) {
+                    int32_t boundary, int vw, bool vec16 = false) {
     // segments of a row of n <= 32 vector columns that fit in a warp: 32 / n
     static constexpr int8_t kSegs[33] = {0, 32, 16, 10, 8, 6, 5, 4, 4, 3, 3, 2, 2, 2, 2, 2, 2,
                                          1, 1,  1,  1,  1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
@@ -153,6 +154,7 @@ inline Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
     g.lastmask = (w & 31) ? ((1u << (w & 31)) - 1u) : kAllOnes;
     g.fill = (boundary == ME_BOUNDARY_WHITE) ? kAllOnes : 0u;
     g.vw = vw;
+    g.vec16 = vw == 4 && vec16;
     g.nv = vw == 4 ? (stride + 3) >> 2 : stride;   // output covers the whole stride
     // narrow rows: segments of exactly nv lanes, as many as fit in a warp
     g.seg_w = g.nv > 32 ? 32 : g.nv;
@@ -196,20 +198,21 @@ inline size_t bulk_arena_bytes(int n, int grid) {
 }
 unsigned int device_fault_flags(bool clear);
 
-// Persistent batch kernel over an uploaded arena.
-cudaError_t launch_batch(const void *arena_dev, int grid, int threads,
-                         int rows_per_lane, cudaStream_t s);
-const void *batch_kernel(int rows_per_lane);   // for graph kernel nodes
+// Persistent batch kernel over an uploaded arena; any: some image of the
+// batch takes 32-bit accesses.
+const void *batch_kernel(int rows_per_lane, bool any);
+unsigned int window_fault_flags(bool clear);
 // Persistent grid of a batch (SMs x ctas_per_sm, capped by occupancy), or
 // for ctas_per_sm == 0 the grid of one chunk per warp over total_tasks tiles.
-int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, int *grid,
-               int *threads);
+int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, bool any,
+               int *grid, int *threads);
 
 // Fill descriptors and the tile-block image table of a batch arena on the
 // host (one pass over the images).  Returns ME_OK or an argument error for
-// descriptor i (*bad = i); *total_tasks = tiles of the batch.
+// descriptor i (*bad = i); *total_tasks = tiles of the batch, *any = some
+// image takes 32-bit accesses.
 int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_arena,
-               int64_t *total_tasks, int *bad);
+               int64_t *total_tasks, bool *any, int *bad);
 
 // How one batch launches under a tile configuration: grid, threads,
 // dynamic shared memory, arena size and kernel.
@@ -219,6 +222,7 @@ struct BatchSetup {
     size_t smem = 0, arena = 0;
     const void *fn = nullptr;
     int stage_words = 0;
+    bool any = false;           // register window: the kernel with 32-bit tiles
 };
 // Neither reads the images' geometry beyond n: descriptors are checked by
 // fill_arena, which also fixes the grid of a one-chunk-per-warp launch.

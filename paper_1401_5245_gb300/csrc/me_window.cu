@@ -14,7 +14,7 @@ namespace me {
 // ------------------------------------------------------------ single image
 // Warp tiles are numbered with the column block fastest, so warps that run
 // together cover whole row bands and share the halo rows in L2.
-template <int VW, int RPT, int MODE>
+template <int VW, int RPT, int MODE, bool V16>
 __global__ void __launch_bounds__(512)
 k_window(Geo g, Outs o, int ntasks) {
     const int lane = threadIdx.x & 31;
@@ -23,30 +23,30 @@ k_window(Geo g, Outs o, int ntasks) {
     for (int t = warp; t < ntasks; t += nwarps) {
         const int cb = t % g.ncb;
         const int rb = t / g.ncb;
-        window_tile<VW, RPT, MODE>(g, o, cb, rb, lane);
+        window_tile<VW, RPT, MODE, V16>(g, o, cb, rb, lane);
     }
 }
 
 using WindowFn = void (*)(Geo, Outs, int);
 
-template <int VW, int MODE>
+template <int VW, int MODE, bool V16>
 static WindowFn pick_rpt(int rpt) {
     switch (rpt) {
-        case 4: return k_window<VW, 4, MODE>;
-        case 8: return k_window<VW, 8, MODE>;
-        case 16: return k_window<VW, 16, MODE>;
-        case 32: return k_window<VW, 32, MODE>;
+        case 4: return k_window<VW, 4, MODE, V16>;
+        case 8: return k_window<VW, 8, MODE, V16>;
+        case 16: return k_window<VW, 16, MODE, V16>;
+        case 32: return k_window<VW, 32, MODE, V16>;
         default: return nullptr;
     }
 }
 
-template <int VW>
+template <int VW, bool V16>
 static WindowFn pick_mode(int mode, int rpt) {
     switch (mode) {
-        case MODE_EDGE: return pick_rpt<VW, MODE_EDGE>(rpt);
-        case MODE_DISPLAY: return pick_rpt<VW, MODE_DISPLAY>(rpt);
-        case MODE_FUND: return pick_rpt<VW, MODE_FUND>(rpt);
-        case MODE_END: return pick_rpt<VW, MODE_END>(rpt);
+        case MODE_EDGE: return pick_rpt<VW, MODE_EDGE, V16>(rpt);
+        case MODE_DISPLAY: return pick_rpt<VW, MODE_DISPLAY, V16>(rpt);
+        case MODE_FUND: return pick_rpt<VW, MODE_FUND, V16>(rpt);
+        case MODE_END: return pick_rpt<VW, MODE_END, V16>(rpt);
         default: return nullptr;
     }
 }
@@ -61,8 +61,9 @@ static int64_t tasks_of(int h, int segs, int ncb, int rpt) {
 
 cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
                           const me_tile_cfg &cfg, cudaStream_t s) {
-    WindowFn fn = (g.vw == 4) ? pick_mode<4>(mode, cfg.rows_per_lane)
-                              : pick_mode<1>(mode, cfg.rows_per_lane);
+    WindowFn fn = g.vw != 4 ? pick_mode<1, false>(mode, cfg.rows_per_lane)
+                  : g.vec16 ? pick_mode<4, true>(mode, cfg.rows_per_lane)
+                            : pick_mode<4, false>(mode, cfg.rows_per_lane);
     if (fn == nullptr) return cudaErrorInvalidValue;
     const int64_t ntasks = tasks_of(g.h, g.segs, g.ncb, cfg.rows_per_lane);
     if (ntasks > INT32_MAX) return cudaErrorInvalidValue;
@@ -94,8 +95,19 @@ cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
 // L1.  A table gives the image of every (1 << block_shift)-th tile; a warp
 // bisects between two entries for the image of its chunk's first tile and
 // walks forward from there.
-template <int RPT>
-__global__ void __launch_bounds__(512)
+// Set by the 128-bit-only batch kernel if it meets an image it cannot take
+// (the host picks the kernel from the same flags, so this stays 0); read and
+// cleared by me_device_faults.
+__device__ unsigned int g_me_window_faults = 0;
+constexpr unsigned int kFaultUnalignedTile = 2u;
+
+// Two 512-thread CTAs per SM for 4 rows per lane (64 registers).  ANY:
+// images whose rows are not whole 16-byte groups (or whose buffers are not
+// 16-byte aligned) may occur, so the kernel also carries the tile that
+// moves four words per lane as 32-bit accesses; batches without such images
+// take the kernel without it, whose registers it would otherwise raise.
+template <int RPT, bool ANY>
+__global__ void __launch_bounds__(512, RPT == 4 ? 2 : 1)
 k_batch(const BatchHeader *__restrict__ hdr) {
     const BDesc *descs = reinterpret_cast<const BDesc *>(hdr + 1);
     const int32_t *block_image = reinterpret_cast<const int32_t *>(descs + hdr->n);
@@ -125,7 +137,8 @@ k_batch(const BatchHeader *__restrict__ hdr) {
             g.nw = d.nw;
             g.lastmask = d.lastmask;
             g.fill = d.fill;
-            g.vw = d.vw;
+            g.vw = d.vw & 0xff;
+            g.vec16 = d.vw >> 8;
             g.nv = d.nv;
             g.seg_w = d.seg_w;
             g.segs = d.segs;
@@ -136,22 +149,24 @@ k_batch(const BatchHeader *__restrict__ hdr) {
             const int local = t - d.task_base;
             const int cb = local % d.ncb;
             const int rb = local / d.ncb;
-            if (d.vw == 4)
-                window_tile<4, RPT, MODE_EDGE>(g, o, cb, rb, lane);
-            else
-                window_tile<1, RPT, MODE_EDGE>(g, o, cb, rb, lane);
+            if (g.vec16)
+                window_tile<4, RPT, MODE_EDGE, true>(g, o, cb, rb, lane);
+            else if constexpr (ANY)
+                window_tile<4, RPT, MODE_EDGE, false>(g, o, cb, rb, lane);
+            else if (lane == 0)
+                atomicOr(&g_me_window_faults, kFaultUnalignedTile);
         }
     }
 }
 
 using BatchFn = void (*)(const BatchHeader *);
 
-static BatchFn pick_batch(int rpt) {
+static BatchFn pick_batch(int rpt, bool any) {
     switch (rpt) {
-        case 4: return k_batch<4>;
-        case 8: return k_batch<8>;
-        case 16: return k_batch<16>;
-        case 32: return k_batch<32>;
+        case 4: return any ? k_batch<4, true> : k_batch<4, false>;
+        case 8: return any ? k_batch<8, true> : k_batch<8, false>;
+        case 16: return any ? k_batch<16, true> : k_batch<16, false>;
+        case 32: return any ? k_batch<32, true> : k_batch<32, false>;
         default: return nullptr;
     }
 }
@@ -197,8 +212,8 @@ int cached_occupancy(const void *fn, int threads, size_t smem, int *out) {
     return ME_OK;
 }
 
-int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, int *grid,
-               int *threads) {
+int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, bool any,
+               int *grid, int *threads) {
     *threads = cfg.cta_threads;
     if (cfg.ctas_per_sm == 0) {
         const int64_t chunks = (total_tasks + chunk_of(cfg) - 1) / chunk_of(cfg);
@@ -208,7 +223,7 @@ int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, i
         return ME_OK;
     }
     int occ = 0;
-    int rc = regs_ctas_per_sm(reinterpret_cast<const void *>(pick_batch(cfg.rows_per_lane)),
+    int rc = regs_ctas_per_sm(reinterpret_cast<const void *>(pick_batch(cfg.rows_per_lane, any)),
                               cfg.cta_threads, &occ);
     if (rc != ME_OK) return rc;
     const int per_sm = std::max(1, std::min(cfg.ctas_per_sm, occ));
@@ -216,17 +231,11 @@ int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, i
     return ME_OK;
 }
 
-cudaError_t launch_batch(const void *arena_dev, int grid, int threads,
-                         int rows_per_lane, cudaStream_t s) {
-    BatchFn fn = pick_batch(rows_per_lane);
-    if (fn == nullptr) return cudaErrorInvalidValue;
-    fn<<<grid, threads, 0, s>>>(static_cast<const BatchHeader *>(arena_dev));
-    return cudaGetLastError();
-}
-
 static void fill_bdesc(const me_desc &d, const me_tile_cfg &cfg, BDesc *out) {
-    const int vw = pick_vw(d.img, d.edge, d.stride_words, cfg.vec_words);
-    Geo g = make_geo(d.img, d.w, d.h, d.stride_words, d.boundary, vw);
+    // batches always take 4 words per lane; vec_words = 1 asks for 32-bit
+    // accesses
+    Geo g = make_geo(d.img, d.w, d.h, d.stride_words, d.boundary, 4,
+                     cfg.vec_words == 4 && vec16_ok(d.img, d.edge, d.stride_words));
     out->img = d.img;
     out->edge = d.edge;
     out->segs = g.segs;
@@ -235,19 +244,20 @@ static void fill_bdesc(const me_desc &d, const me_tile_cfg &cfg, BDesc *out) {
     out->nw = g.nw;
     out->lastmask = g.lastmask;
     out->fill = g.fill;
-    out->vw = g.vw;
+    out->vw = g.vw | (g.vec16 << 8);     // words per lane, and 128-bit accesses
     out->seg_w = g.seg_w;
     out->ncb = g.ncb;
     out->nv = g.nv;
 }
 
 int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_arena,
-               int64_t *total_tasks, int *bad) {
+               int64_t *total_tasks, bool *any, int *bad) {
     BatchHeader *hdr = static_cast<BatchHeader *>(host_arena);
     BDesc *bd = reinterpret_cast<BDesc *>(hdr + 1);
     int32_t *block_image = reinterpret_cast<int32_t *>(bd + n);
     std::memset(hdr, 0, sizeof(*hdr));
     int64_t total = 0, bytes = 0;
+    bool words32 = false;       // some image takes 32-bit accesses
     for (int i = 0; i < n; ++i) {
         const me_desc &d = descs[i];
         int rc = check_image_args(d.img, d.edge, d.w, d.h, d.stride_words, d.boundary);
@@ -256,6 +266,7 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_a
             return rc;
         }
         fill_bdesc(d, cfg, &bd[i]);
+        words32 |= (bd[i].vw >> 8) == 0;
         const int64_t nt = tasks_of(bd[i].h, bd[i].segs, bd[i].ncb, cfg.rows_per_lane);
         if (total + nt > INT32_MAX) {
             if (bad) *bad = i;
@@ -285,13 +296,27 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_a
     }
     block_image[b] = n - 1;
     if (total_tasks) *total_tasks = total;
+    if (any) *any = words32;
     return ME_OK;
+}
+
+unsigned int window_fault_flags(bool clear) {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_me_window_faults, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (clear) {
+        const unsigned int z = 0;
+        cudaMemcpyToSymbol(g_me_window_faults, &z, sizeof(z));
+    }
+    return v;
 }
 
 }  // namespace me
 
 namespace me {
-const void *batch_kernel(int rows_per_lane) {
-    return reinterpret_cast<const void *>(pick_batch(rows_per_lane));
+const void *batch_kernel(int rows_per_lane, bool any) {
+    return reinterpret_cast<const void *>(pick_batch(rows_per_lane, any));
 }
 }  // namespace me
