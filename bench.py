@@ -712,6 +712,21 @@ def run_ours(args, rank, world, local_rank):
                                 "tile_cfg": _lib.me_get_tile_cfg(0).as_dict()}
         extra["staged_32768"] = {"gpixel_s": round(w * h / t_staged1 / 1e9, 1),
                                  "us": round(t_staged1 * 1e6, 2)}
+
+        # in place (the edge map over the image; the work does not depend on
+        # the bits, so the rotating buffers are simply overwritten again)
+        def inplace1():
+            i = k[0] % 3
+            k[0] += 1
+            rc = lib.me_edges_inplace(xs[i].data_ptr(), w, h, 1024, 0, stream.cuda_stream)
+            if rc != 0:
+                raise _lib.MeError(rc, "me_edges_inplace")
+        inplace1()
+        t_inplace = time_events(inplace1, 30, stream)
+        extra["inplace_32768"] = {"gpixel_s": round(w * h / t_inplace / 1e9, 1),
+                                  "gb_s": round(b1 / t_inplace / 1e9, 1),
+                                  "frac_of_peak": round(b1 / t_inplace / 1e9 / peak, 4),
+                                  "us": round(t_inplace * 1e6, 2)}
         del xs, ys
 
     if not args.quick:

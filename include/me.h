@@ -176,6 +176,27 @@ int me_end_points(const uint32_t *img, int32_t w, int32_t h,
                   int32_t stride_words, uint32_t *out, int32_t boundary,
                   me_stream_t stream);
 
+/*
+ * me_edges computed in place: the edge map replaces the image in img (the
+ * result the paper draws over its input, with no second buffer).  Each row
+ * is overwritten only after every read of its original bits: the image is
+ * cut into bands of rows, one CTA per band walking it top to bottom, and
+ * the two rows on either side of every band seam are first copied to
+ * scratch the library takes from CUDA's stream-ordered allocator on
+ * `stream` and returns when the call's work is done
+ * (2 * (bands - 1) * stride_words * 4 bytes, bands = about 4 per SM, at
+ * least 32 rows each; none for a single band).
+ *
+ * img           device pointer, 4-byte aligned; 128-bit accesses when it
+ *               is 16-byte aligned and stride_words % 4 == 0.
+ * w, h, stride_words, boundary, stream   as me_edges.
+ * Rows wider than 2048 groups of 4 words (262,144 pixels) return
+ * ME_ERR_TOO_BIG with nothing enqueued; failure to get the scratch returns
+ * ME_ERR_CUDA with nothing enqueued.
+ */
+int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t stride_words,
+                     int32_t boundary, me_stream_t stream);
+
 /* ---- many images in one launch ----------------------------------------- */
 
 typedef struct me_desc {

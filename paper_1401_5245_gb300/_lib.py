@@ -90,6 +90,7 @@ PROTOTYPES = {
                                             c_vp, c_vp, c_i32, c_vp]),
     "me_edges_display": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
     "me_end_points": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
+    "me_edges_inplace": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_i32, c_vp]),
     "me_edges_batch": (ctypes.c_int, [ctypes.POINTER(me_desc), c_i32, c_vp]),
     "me_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(me_desc), c_i32, c_vp,
                                             ctypes.POINTER(c_vp)]),
@@ -173,6 +174,11 @@ def me_edges(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:
 def me_edges_staged(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:
     return load().me_edges_staged(ptr(img), w, h, stride_words, ptr(edge), boundary,
                                   stream_handle(stream))
+
+
+def me_edges_inplace(img, w, h, stride_words, boundary=0, stream=None) -> int:
+    return load().me_edges_inplace(ptr(img), w, h, stride_words, boundary,
+                                   stream_handle(stream))
 
 
 def me_edges_staged_static(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:

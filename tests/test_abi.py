@@ -72,6 +72,11 @@ def test_argument_errors_without_a_gpu(lib):
     assert L.me_edges(a, 64, 100, 2, a + 400, 0, None) == ALIAS
     assert L.me_edges_staged(a, 64, 100, 2, a + 8, 0, None) == ALIAS
     assert L.me_fundamental_edges(a, 8, 8, 1, b, b, b + 64, b + 128, 0, None) == ALIAS
+    assert L.me_edges_inplace(None, 8, 8, 1, 0, None) == ARG
+    assert L.me_edges_inplace(a, 0, 8, 1, 0, None) == ARG             # w
+    assert L.me_edges_inplace(a, 64, 8, 1, 0, None) == ARG            # stride
+    assert L.me_edges_inplace(a, 8, 8, 1, 3, None) == ARG             # boundary
+    assert L.me_edges_inplace(a + 2, 8, 8, 1, 0, None) == ARG         # not word aligned
     assert L.me_edges_batch(None, -1, None) == ARG
     assert L.me_edges_batch(None, 0, None) == lib.C["ME_OK"]
     bad = lib.make_descs([(a, a, 8, 8, 1, 0)])
