@@ -178,21 +178,23 @@ int me_end_points(const uint32_t *img, int32_t w, int32_t h,
 
 /*
  * me_edges computed in place: the edge map replaces the image in img (the
- * result the paper draws over its input, with no second buffer).  Each row
- * is overwritten only after every read of its original bits: the image is
- * cut into bands of rows, one CTA per band walking it top to bottom, and
- * the two rows on either side of every band seam are first copied to
- * scratch the library takes from CUDA's stream-ordered allocator on
- * `stream` and returns when the call's work is done
+ * result the paper draws over its input, with no second buffer of the
+ * caller's).  Images up to 32 MiB (h * stride_words * 4 bytes; the environment
+ * variable ME_INPLACE_COPY_MAX, read on every call, sets another limit in
+ * bytes) are copied whole to scratch and computed from the copy.  Larger ones are cut into
+ * bands of rows, one CTA per band walking it top to bottom so that each row
+ * is overwritten only after every read of its original bits, and the two
+ * rows on either side of every band seam are first copied to scratch
  * (2 * (bands - 1) * stride_words * 4 bytes, bands = about 4 per SM, at
- * least 32 rows each; none for a single band).
+ * least 32 rows each).  Scratch comes from CUDA's stream-ordered allocator
+ * on `stream` and is returned when the call's work is done.
  *
  * img           device pointer, 4-byte aligned; 128-bit accesses when it
  *               is 16-byte aligned and stride_words % 4 == 0.
  * w, h, stride_words, boundary, stream   as me_edges.
- * Rows wider than 2048 groups of 4 words (262,144 pixels) return
- * ME_ERR_TOO_BIG with nothing enqueued; failure to get the scratch returns
- * ME_ERR_CUDA with nothing enqueued.
+ * Above the copy limit, rows wider than 2048 groups of 4 words (262,144
+ * pixels) return ME_ERR_TOO_BIG with nothing enqueued; failure to get the
+ * scratch returns ME_ERR_CUDA with nothing enqueued.
  */
 int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t stride_words,
                      int32_t boundary, me_stream_t stream);

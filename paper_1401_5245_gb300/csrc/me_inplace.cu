@@ -3,30 +3,53 @@
 // Every output row needs the original rows above and below it, so a row may
 // be overwritten only once nobody still has to read it.  The image is cut
 // into bands of band_rows rows; one CTA owns a band across the whole row
-// width and walks it top to bottom.  Each thread owns up to C vector
-// columns of 4 words and reads and writes global memory only there: at row
-// y it holds the original rows y-1 and y in registers and has already
-// loaded the rows below up to y+PF+1, computes row y and overwrites it.
-// The words just left and right of each thread's columns (the neighbouring
-// columns' words of row y) are exchanged through shared memory, one
-// barrier per row, double-buffered, so within a band no thread ever reads
-// a row another thread has overwritten.
+// width and walks it top to bottom, G rows at a time.  Each thread owns up
+// to C vector columns of 4 words and copies its columns of the rows ahead
+// (cp.async, one commit group per row) into a ring of Q rows in shared
+// memory.  Per group: wait for this thread's copies up to the group's last
+// row below, one barrier (everyone's copies are then visible, and everyone
+// has finished the previous group, whose oldest ring slots are refilled
+// next), issue the next G rows, then compute the group's rows from the ring
+// -- own columns and the neighbouring columns' end words alike -- and
+// overwrite them in global memory.  A thread reads global memory only at
+// its own columns, and each row's copy has landed before the row is
+// overwritten.
 //
 // Between CTAs the only shared rows are at the band seams: the last row of
 // a band is the row above the next band, and the first row of a band is the
 // row below the previous one.  A first kernel copies those two rows of
 // every seam into scratch before any band starts, and bands read their
 // outer halo rows from there.
+//
+// A band is one row wide in threads and a chain of memory round trips in
+// time, so images of a few bands per SM leave the GPU mostly idle.  Images
+// up to kCopyMax bytes (or ME_INPLACE_COPY_MAX) are instead copied to
+// scratch whole and computed by
+// the out-of-place kernel from the copy onto the image: twice the traffic,
+// but all of it parallel (measured on GB300: a 4096 x 4096 image in about
+// 7 us against 20 us by bands; at 16384 x 16384 the two meet).
 #include <algorithm>
+#include <cstdlib>
+#include <mutex>
 
 #include "me_internal.h"
+#include "me_ptx.cuh"
 
 namespace me {
 
 namespace {
 
-constexpr int kIpPF = 2;                // rows loaded ahead of the next row
 constexpr int kIpMaxThreads = 1024;
+constexpr size_t kCopyMax = 32ull << 20;   // whole-image copy up to 32 MiB
+
+// The whole-image copy limit: ME_INPLACE_COPY_MAX (bytes) if set, else kCopyMax.
+size_t copy_max() {
+    const char *v = std::getenv("ME_INPLACE_COPY_MAX");
+    if (v == nullptr || *v == 0) return kCopyMax;
+    char *end = nullptr;
+    const unsigned long long x = std::strtoull(v, &end, 10);
+    return (end != nullptr && *end == 0) ? (size_t)x : kCopyMax;
+}
 
 struct IpGeo {
     uint32_t *img;
@@ -49,116 +72,126 @@ __device__ __forceinline__ const uint32_t *ip_row(const IpGeo &g, int b, int y0,
     return nullptr;
 }
 
-// Row y's 4 words at column c0, outside words and padding replaced by the
-// boundary colour.
-template <bool V16>
-__device__ __forceinline__ uint4 ip_load(const IpGeo &g, const uint32_t *row, int c0,
-                                         bool active) {
-    uint32_t raw[4] = {0u, 0u, 0u, 0u};
-    if (row != nullptr && active) {
-        if constexpr (V16) {
-            if (c0 < g.nw) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(row + c0);
-                raw[0] = v.x; raw[1] = v.y; raw[2] = v.z; raw[3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (c0 + k < g.nw) raw[k] = row[c0 + k];
-        }
-    }
-    uint32_t o[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t keep = row != nullptr ? ip_keep(g, c0 + k) : 0u;
-        o[k] = (raw[k] & keep) | (g.fill & ~keep);
-    }
-    return make_uint4(o[0], o[1], o[2], o[3]);
-}
-
-__device__ __forceinline__ uint32_t q_at(const uint4 &q, int i) {
-    return i == 0 ? q.x : i == 1 ? q.y : i == 2 ? q.z : q.w;
-}
-
-template <int C, bool V16>
+template <int C, bool V16, int Q, int G>
 __global__ void __launch_bounds__(kIpMaxThreads)
 k_inplace(IpGeo g) {
-    // first and last word of every vector column of the current row
-    __shared__ uint32_t s_first[2][2 * kIpMaxThreads], s_last[2][2 * kIpMaxThreads];
+    static_assert(Q >= 2 * G + 2, "the ring holds a group, its halo rows and the rows ahead");
+    extern __shared__ uint4 s_ring[];              // [Q][C * T]
     const int b = blockIdx.x;
     const int y0 = b * g.band_rows;
     const int y1 = min(y0 + g.band_rows, g.h);
     const int T = blockDim.x;
+    const int CT = C * T;
 
-    int c0[C];
+    int vcol[C];
     bool active[C];
 #pragma unroll
     for (int k = 0; k < C; ++k) {
-        const int v = threadIdx.x + k * T;
-        active[k] = v < g.nv;
-        c0[k] = v * 4;
+        vcol[k] = threadIdx.x + k * T;
+        active[k] = vcol[k] < g.nv;
     }
-    auto load = [&](int k, int y) {
-        return ip_load<V16>(g, ip_row(g, b, y0, y1, y), c0[k], active[k]);
+    // ring slot of row r (r >= y0 - 1)
+    auto slot = [&](int r) { return (r - y0 + 1) % Q; };
+    // this thread's columns of row r into the ring (nothing for rows
+    // without a source); one commit group per row in any case
+    auto issue = [&](int r) {
+        const uint32_t *row = ip_row(g, b, y0, y1, r);
+        if (row != nullptr) {
+            uint4 *dst = s_ring + slot(r) * CT;
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                const int c0 = vcol[k] * 4;
+                if (!active[k]) continue;
+                if constexpr (V16) {
+                    if (c0 < g.nw) cp_async16(dst + vcol[k], row + c0);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (c0 + i < g.nw)
+                            cp_async4(reinterpret_cast<uint32_t *>(dst + vcol[k]) + i, row + c0 + i);
+                }
+            }
+        }
+        cp_async_commit();
     };
-
-    uint4 up[C], cur[C], q[C][kIpPF + 1];
+    // this thread's keep masks: its 4 words, and the words just beside them
+    uint32_t keep[C][4], keep_l[C], keep_r[C];
 #pragma unroll
     for (int k = 0; k < C; ++k) {
-        up[k] = load(k, y0 - 1);
-        cur[k] = load(k, y0);
 #pragma unroll
-        for (int i = 0; i <= kIpPF; ++i) q[k][i] = load(k, y0 + 1 + i);
+        for (int i = 0; i < 4; ++i) keep[k][i] = ip_keep(g, vcol[k] * 4 + i);
+        keep_l[k] = ip_keep(g, vcol[k] * 4 - 1);
+        keep_r[k] = ip_keep(g, vcol[k] * 4 + 4);
     }
+    const uint4 fill4 = make_uint4(g.fill, g.fill, g.fill, g.fill);
+    auto fix = [&](uint32_t raw, uint32_t keep) { return (raw & keep) | (g.fill & ~keep); };
+    auto fix4 = [&](uint4 r, const uint32_t (&kp)[4]) {
+        return make_uint4(fix(r.x, kp[0]), fix(r.y, kp[1]), fix(r.z, kp[2]), fix(r.w, kp[3]));
+    };
 
-    int buf = 0;
+    for (int r = y0 - 1; r <= y0 + Q - G - 2; ++r) issue(r);
+
+    const int lane = threadIdx.x & 31;
 #pragma unroll 1
-    for (int y = y0; y < y1; y += kIpPF + 1) {
+    for (int y = y0; y < y1; y += G) {
+        cp_async_wait<Q - 2 * G - 2>();            // own copies of rows <= y + G
+        __syncthreads();
+        for (int r = y + Q - G - 1; r <= y + Q - 2; ++r) issue(r);
+        int s_up = slot(y - 1);                    // ring slots of rows y - 1, y, y + 1
+        int s_cur = s_up + 1 == Q ? 0 : s_up + 1;
 #pragma unroll
-        for (int j = 0; j <= kIpPF; ++j) {
+        for (int j = 0; j < G; ++j) {
             const int yy = y + j;
             if (yy >= y1) break;
+            const int s_dn = s_cur + 1 == Q ? 0 : s_cur + 1;
+            // rows y0 - 1 .. y1 all have a source when they lie in the image
+            const bool have_up = yy >= 1, have_dn = yy + 1 < g.h;
 #pragma unroll
             for (int k = 0; k < C; ++k) {
-                const int v = threadIdx.x + k * T;
-                s_first[buf][v] = cur[k].x;
-                s_last[buf][v] = cur[k].w;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < C; ++k) {
-                const uint4 dn = q[k][j];
-                // rows up to y1 only: those further down belong to other bands
-                q[k][j] = load(k, yy + kIpPF + 2 <= y1 ? yy + kIpPF + 2 : -2);
-                const int v = threadIdx.x + k * T;
-                const uint32_t prev = v > 0 ? s_last[buf][v - 1] : g.fill;
-                const uint32_t next = v + 1 < C * T ? s_first[buf][v + 1] : g.fill;
+                const int v = vcol[k];
+                const uint4 c = fix4(s_ring[s_cur * CT + v], keep[k]);
+                const uint4 u = have_up ? fix4(s_ring[s_up * CT + v], keep[k]) : fill4;
+                const uint4 d = have_dn ? fix4(s_ring[s_dn * CT + v], keep[k]) : fill4;
+                // the words beside: warp neighbours, the ring at the warp's ends
+                uint32_t lw = __shfl_up_sync(0xFFFFFFFFu, c.w, 1);
+                uint32_t rw = __shfl_down_sync(0xFFFFFFFFu, c.x, 1);
+                if (lane == 0)
+                    lw = v > 0 ? fix(reinterpret_cast<const uint32_t *>(
+                                         s_ring + s_cur * CT + v - 1)[3], keep_l[k])
+                               : g.fill;
+                if (lane == 31)
+                    rw = v + 1 < CT ? fix(s_ring[s_cur * CT + v + 1].x, keep_r[k]) : g.fill;
+                const uint32_t cw[6] = {lw, c.x, c.y, c.z, c.w, rw};
+                const uint32_t uw[4] = {u.x, u.y, u.z, u.w}, dw[4] = {d.x, d.y, d.z, d.w};
                 uint32_t e[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const uint32_t x = q_at(cur[k], i);
-                    const uint32_t pv = i == 0 ? prev : q_at(cur[k], i - 1);
-                    const uint32_t nx = i == 3 ? next : q_at(cur[k], i + 1);
-                    const uint32_t L = __funnelshift_l(pv, x, 1);   // I(x-1, y)
-                    const uint32_t R = __funnelshift_r(x, nx, 1);   // I(x+1, y)
-                    e[i] = ~x & (L | R | q_at(up[k], i) | q_at(dn, i)) & ip_keep(g, c0[k] + i);
+                    const uint32_t x = cw[1 + i];
+                    const uint32_t L = __funnelshift_l(cw[i], x, 1);       // I(x-1, y)
+                    const uint32_t R = __funnelshift_r(x, cw[2 + i], 1);   // I(x+1, y)
+                    e[i] = ~x & (L | R | uw[i] | dw[i]) & keep[k][i];
                 }
                 if (active[k]) {
-                    uint32_t *out = g.img + (size_t)yy * (size_t)g.stride + c0[k];
+                    uint32_t *out = g.img + (size_t)yy * (size_t)g.stride + v * 4;
                     if constexpr (V16) {
                         *reinterpret_cast<uint4 *>(out) = make_uint4(e[0], e[1], e[2], e[3]);
                     } else {
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            if (c0[k] + i < g.stride) out[i] = e[i];
+                            if (v * 4 + i < g.stride) out[i] = e[i];
                     }
                 }
-                up[k] = cur[k];
-                cur[k] = dn;
             }
-            buf ^= 1;
+            s_up = s_cur;
+            s_cur = s_dn;
         }
     }
+    cp_async_wait<0>();
+}
+
+template <int C, int Q>
+constexpr size_t inplace_smem(int threads) {
+    return (size_t)Q * C * threads * sizeof(uint4);
 }
 
 // Rows on both sides of every seam into scratch: seam k = rows
@@ -173,9 +206,18 @@ __global__ void k_inplace_seams(IpGeo g, uint32_t *seam) {
     }
 }
 
-template <int C, bool V16>
+template <int C, bool V16, int Q, int G>
 cudaError_t launch_inplace(const IpGeo &g, int threads, cudaStream_t s) {
-    k_inplace<C, V16><<<g.nbands, threads, 0, s>>>(g);
+    // the ring exceeds the default 48 KiB for wide rows; raise the limit once
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(k_inplace<C, V16, Q, G>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)inplace_smem<C, Q>(kIpMaxThreads));
+    });
+    if (attr != cudaSuccess) return attr;
+    k_inplace<C, V16, Q, G><<<g.nbands, threads, inplace_smem<C, Q>(threads), s>>>(g);
     return cudaGetLastError();
 }
 
@@ -194,6 +236,27 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
         return ME_ERR_ARG;
     int rc = check_device_ptr(img);
     if (rc != ME_OK) return rc;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const size_t img_bytes = (size_t)h * (size_t)stride_words * 4;
+    if (img_bytes <= copy_max()) {
+        uint32_t *copy = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&copy), img_bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return record_cuda(e);
+        }
+        e = cudaMemcpyAsync(copy, img, img_bytes, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) {
+            rc = me_edges(copy, w, h, stride_words, img, boundary, stream);
+            if (rc != ME_OK) e = cudaErrorLaunchFailure;
+        }
+        const cudaError_t f = cudaFreeAsync(copy, s);
+        if (e != cudaSuccess || f != cudaSuccess) {
+            cudaGetLastError();
+            return rc != ME_OK ? rc : record_cuda(e != cudaSuccess ? e : f);
+        }
+        return ME_OK;
+    }
     DevInfo di;
     if ((rc = device_info(&di)) != ME_OK) return rc;
     const Geo geo = make_geo(img, w, h, stride_words, boundary, 4,
@@ -218,7 +281,6 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
     g.band_rows = (int32_t)std::max<int64_t>(32, (h + want - 1) / want);
     g.nbands = (int32_t)(((int64_t)h + g.band_rows - 1) / g.band_rows);
 
-    const cudaStream_t s = (cudaStream_t)stream;
     uint32_t *seam = nullptr;
     cudaError_t e = cudaSuccess;
     if (g.nbands > 1) {
@@ -233,11 +295,14 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
+        // rows of up to 1024 columns: a 12-row ring, 4 rows per barrier;
+        // wider ones: 6 rows, 2 per barrier (at most 192 KiB either way)
         if (geo.vec16)
-            e = C == 1 ? launch_inplace<1, true>(g, threads, s) : launch_inplace<2, true>(g, threads, s);
+            e = C == 1 ? launch_inplace<1, true, 12, 4>(g, threads, s)
+                       : launch_inplace<2, true, 6, 2>(g, threads, s);
         else
-            e = C == 1 ? launch_inplace<1, false>(g, threads, s)
-                       : launch_inplace<2, false>(g, threads, s);
+            e = C == 1 ? launch_inplace<1, false, 12, 4>(g, threads, s)
+                       : launch_inplace<2, false, 6, 2>(g, threads, s);
     }
     if (seam != nullptr) {
         const cudaError_t f = cudaFreeAsync(seam, s);

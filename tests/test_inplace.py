@@ -23,6 +23,14 @@ def built():
     _lib.load()
 
 
+@pytest.fixture(autouse=True, params=["bands", "copy"])
+def route(request, monkeypatch):
+    """Every case both ways: bands of rows walked in place (copy limit 0)
+    and the whole-image copy (limit above every test image)."""
+    monkeypatch.setenv("ME_INPLACE_COPY_MAX", "0" if request.param == "bands" else str(1 << 40))
+    return request.param
+
+
 def sync():
     import torch
     torch.cuda.synchronize()
@@ -88,11 +96,14 @@ def test_matches_out_of_place_on_a_large_image():
     assert torch.equal(x, ref)
 
 
-def test_rows_too_wide_and_bad_arguments():
+def test_rows_too_wide_and_bad_arguments(route):
+    """Bands take rows of at most 2048 groups of 4 words; the whole-image
+    copy has no such limit."""
     import torch
     L = _lib.load()
     x = torch.zeros(8200, dtype=torch.int32, device="cuda")
-    assert L.me_edges_inplace(x.data_ptr(), 262145, 1, 8193, 0, None) == _lib.C["ME_ERR_TOO_BIG"]
+    want = _lib.C["ME_ERR_TOO_BIG"] if route == "bands" else 0
+    assert L.me_edges_inplace(x.data_ptr(), 262145, 1, 8193, 0, None) == want
     assert L.me_edges_inplace(x.data_ptr(), 262144, 1, 8192, 0, None) == 0
     host = np.zeros(64, dtype=np.uint32)
     assert L.me_edges_inplace(host.ctypes.data, 32, 2, 1, 0, None) == _lib.C["ME_ERR_ARG"]
