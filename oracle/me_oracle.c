@@ -144,3 +144,20 @@ int me_oracle_end_points(const uint8_t *img, int w, int h, int boundary,
     }
     return 0;
 }
+
+/*
+ * Thresholding ahead of the method: Section 7 makes a grey photograph
+ * binary before finding its edges but names no rule.  Reading taken: one
+ * global threshold t, a pixel is white (1) where its grey value is at least
+ * t and black (0) below it.  grey is u8[h][pitch], pitch >= w bytes; out is
+ * u8[h][w].  t <= 0 makes every pixel white, t > 255 every pixel black.
+ */
+int me_oracle_threshold(const uint8_t *grey, int w, int h, int pitch, int t, uint8_t *out)
+{
+    if (grey == NULL || out == NULL || w < 0 || h < 0 || pitch < w)
+        return -1;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x)
+            out[(size_t)y * w + x] = (uint8_t)((int)grey[(size_t)y * pitch + x] >= t);
+    return 0;
+}

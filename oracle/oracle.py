@@ -61,9 +61,10 @@ def _load():
             lib.me_oracle_fundamental.argtypes = [u8p, i32, i32, i32, u8p, u8p,
                                                   u8p, u8p]
             lib.me_oracle_end_points.argtypes = [u8p, i32, i32, i32, u8p]
+            lib.me_oracle_threshold.argtypes = [u8p, i32, i32, i32, i32, u8p]
             for f in (lib.me_oracle_mask, lib.me_oracle_edges,
                       lib.me_oracle_edges_many, lib.me_oracle_fundamental,
-                      lib.me_oracle_end_points):
+                      lib.me_oracle_end_points, lib.me_oracle_threshold):
                 f.restype = i32
             _lib = lib
     return _lib
@@ -128,6 +129,18 @@ def end_points(img, boundary: int = 0) -> np.ndarray:
     out = np.empty_like(a)
     _check(_load().me_oracle_end_points(_ptr(a), a.shape[1], a.shape[0],
                                         int(boundary), _ptr(out)))
+    return out
+
+
+def threshold(grey, t: int) -> np.ndarray:
+    """Section 7's grey photograph made binary (the paper names no rule):
+    1 (white) where grey >= t, 0 (black) below."""
+    a = np.ascontiguousarray(grey, dtype=np.uint8)
+    if a.ndim != 2:
+        raise ValueError("expected a 2-D grey image")
+    out = np.empty_like(a)
+    _check(_load().me_oracle_threshold(_ptr(a), a.shape[1], a.shape[0], a.shape[1],
+                                       int(t), _ptr(out)))
     return out
 
 

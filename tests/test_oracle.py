@@ -260,6 +260,34 @@ def test_end_points_hand_cases():
 
 
 # ---------------------------------------------------------------------------
+# thresholding ahead of the method (Section 7)
+# ---------------------------------------------------------------------------
+
+def test_threshold_extremes_and_hand_case():
+    grey = np.array([[0, 127, 128, 255]], dtype=np.uint8)
+    assert O.threshold(grey, 128).tolist() == [[0, 0, 1, 1]]
+    assert O.threshold(grey, 0).tolist() == [[1, 1, 1, 1]]
+    assert O.threshold(grey, 256).tolist() == [[0, 0, 0, 0]]
+    assert O.threshold(grey, 255).tolist() == [[0, 0, 0, 1]]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_threshold_counts_match_the_histogram(seed):
+    """White pixels at threshold t = the histogram's mass at t and above,
+    for every t; whites only shrink as t grows."""
+    g = np.random.default_rng(seed)
+    grey = g.integers(0, 256, (37, 53), dtype=np.uint8)
+    tail = np.cumsum(np.bincount(grey.ravel(), minlength=256)[::-1])[::-1]
+    prev = None
+    for t in range(0, 257):
+        b = O.threshold(grey, t)
+        assert b.sum() == (tail[t] if t < 256 else 0)
+        if prev is not None:
+            assert not (b & (1 - prev)).any()
+        prev = b
+
+
+# ---------------------------------------------------------------------------
 # planted mistakes must fail a pin
 # ---------------------------------------------------------------------------
 
@@ -273,6 +301,8 @@ MUTATIONS = {
     "mask not inverted": ("(uint8_t)(!p && (n2", "(uint8_t)(p && (n2"),
     "left/right swapped": ("left[i]  = (uint8_t)(m && pixel(img, w, h, x - 1, y, o));",
                            "left[i]  = (uint8_t)(m && pixel(img, w, h, x + 1, y, o));"),
+    "threshold strict": ("(int)grey[(size_t)y * pitch + x] >= t", "(int)grey[(size_t)y * pitch + x] > t"),
+    "threshold pitch ignored": ("grey[(size_t)y * pitch + x]", "grey[(size_t)y * w + x]"),
 }
 
 
@@ -315,6 +345,13 @@ def _pins_pass(lib):
                 return False
     img = np.array([[1, 0, 0, 1]], dtype=np.uint8)
     if left(img, 1).tolist() != [[0, 1, 0, 0]]:
+        return False
+    # thresholding: the hand case, and a pitch wider than the row
+    grey = np.array([[0, 127, 128, 255, 9, 9], [200, 3, 128, 127, 9, 9]], dtype=np.uint8)
+    out = np.zeros((2, 4), dtype=np.uint8)
+    lib.me_oracle_threshold(ctypes.c_void_p(grey.ctypes.data), 4, 2, 6, 128,
+                            ctypes.c_void_p(out.ctypes.data))
+    if out.tolist() != [[0, 0, 1, 1], [1, 0, 1, 0]]:
         return False
     return True
 
