@@ -344,6 +344,45 @@ def c1_leg(lib_mod, stream, seeds=(0, 1, 2), reps=2000):
                 v["us_per_call_back_to_back"] for v in out.values()) / 1e3, 2)}
 
 
+def threshold_leg(lib_mod, stream, peak):
+    """Section 7's front end fused with the method: an 8192 x 8192 grey image
+    (64 MiB, 8 bits per pixel) thresholded at 128 and its edges found in one
+    pass, with and without the packed binary image; 3 rotating inputs."""
+    import torch
+    from oracle import oracle
+    w = h = 8192
+    g = np.random.default_rng(0)
+    yy, xx = np.mgrid[0:256, 0:w]
+    tile = np.clip((np.sin(xx / 7.0) + np.cos(yy / 11.0)) * 60 + 128 + g.normal(0, 25, (256, w)),
+                   0, 255).astype(np.uint8)
+    grey = np.tile(tile, (h // 256, 1))
+    xs = [torch.from_numpy(grey).cuda() for _ in range(3)]
+    edge = torch.empty((h, w // 32), dtype=torch.int32, device="cuda")
+    binary = torch.empty_like(edge)
+    lib_mod.check(lib_mod.me_threshold_edges(xs[0], w, h, w, 128, edge, w // 32, binary, 0, stream))
+    torch.cuda.synchronize()
+    from paper_1401_5245_gb300 import synth
+    want = oracle.edges(oracle.threshold(grey[:300], 128), 0)
+    got = synth.unpack(edge[:299].cpu().numpy().view(np.uint32), w)
+    exact = bool(np.array_equal(got, want[:299]))
+    out = {"exact_first_299_rows": exact}
+    for name, b in (("edge", None), ("edge_and_binary", binary)):
+        k = [0]
+
+        def one():
+            i = k[0] % 3
+            k[0] += 1
+            lib_mod.check(lib_mod.me_threshold_edges(xs[i], w, h, w, 128, edge, w // 32, b, 0,
+                                                     stream))
+        one()
+        t = time_events(one, 30, stream)
+        nbytes = w * h + w * h // 8 * (1 if b is None else 2)
+        out[name] = {"us": round(t * 1e6, 2), "gpixel_s": round(w * h / t / 1e9, 1),
+                     "gb_s": round(nbytes / t / 1e9, 1),
+                     "frac_of_peak": round(nbytes / t / 1e9 / peak, 4)}
+    return out
+
+
 def unpadded_leg(lib_mod, stream, peak):
     """The uneven batch with stride = ceil(w / 32) (no padding to 16 bytes):
     rows are not 16-byte groups, so every image takes the 32-bit path."""
@@ -730,6 +769,7 @@ def run_ours(args, rank, world, local_rank):
         del xs, ys
 
     if not args.quick:
+        extra["threshold_8192"] = threshold_leg(_lib, stream, peak)
         extra["c1_256"] = c1_leg(_lib, stream)
         extra["data_independence_4096"] = density_leg(_lib, stream)
         extra["unpadded_batch"] = unpadded_leg(_lib, stream, peak)

@@ -199,6 +199,30 @@ int me_end_points(const uint32_t *img, int32_t w, int32_t h,
 int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t stride_words,
                      int32_t boundary, me_stream_t stream);
 
+/*
+ * Thresholding fused ahead of the method.  Section 7 makes a grey
+ * photograph binary and then finds its edges, but names no rule; one global
+ * threshold is taken: pixel (x, y) is white where
+ * grey[y * pitch_bytes + x] >= threshold and black below it, and edge is
+ * me_edges of that binary image.  One pass: 8 bits of grey read per pixel,
+ * 1 bit written (2 with binary).
+ *
+ * grey          device u8[h][pitch_bytes], pitch_bytes >= w; 128-bit loads
+ *               when grey and pitch_bytes are 16-byte aligned, byte loads
+ *               otherwise.
+ * threshold     <= 0 makes every pixel white, > 255 every pixel black.
+ * edge          device output, h rows of stride_words words
+ *               (>= ceil(w / 32)), 4-byte aligned, layout and zeroed padding
+ *               as me_edges.
+ * binary        NULL, or a device output of the same layout that receives
+ *               the thresholded image packed.
+ * boundary, stream   as me_edges.
+ * grey, edge and binary must not overlap (ME_ERR_ALIAS).
+ */
+int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int32_t pitch_bytes,
+                       int32_t threshold, uint32_t *edge, int32_t stride_words,
+                       uint32_t *binary, int32_t boundary, me_stream_t stream);
+
 /* ---- many images in one launch ----------------------------------------- */
 
 typedef struct me_desc {

@@ -91,6 +91,8 @@ PROTOTYPES = {
     "me_edges_display": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
     "me_end_points": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp]),
     "me_edges_inplace": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_i32, c_vp]),
+    "me_threshold_edges": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_i32, c_vp, c_i32,
+                                          c_vp, c_i32, c_vp]),
     "me_edges_batch": (ctypes.c_int, [ctypes.POINTER(me_desc), c_i32, c_vp]),
     "me_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(me_desc), c_i32, c_vp,
                                             ctypes.POINTER(c_vp)]),
@@ -179,6 +181,12 @@ def me_edges_staged(img, w, h, stride_words, edge, boundary=0, stream=None) -> i
 def me_edges_inplace(img, w, h, stride_words, boundary=0, stream=None) -> int:
     return load().me_edges_inplace(ptr(img), w, h, stride_words, boundary,
                                    stream_handle(stream))
+
+
+def me_threshold_edges(grey, w, h, pitch_bytes, threshold, edge, stride_words, binary=None,
+                       boundary=0, stream=None) -> int:
+    return load().me_threshold_edges(ptr(grey), w, h, pitch_bytes, threshold, ptr(edge),
+                                     stride_words, ptr(binary), boundary, stream_handle(stream))
 
 
 def me_edges_staged_static(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:
