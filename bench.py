@@ -805,7 +805,9 @@ def run_ours(args, rank, world, local_rank):
 def run_profile_case(case: str, launches: int, cfg: str | None = None):
     """A few launches of one kernel on a case small enough for an ncu
     capture (inputs still larger than L2): 'batch' = the 4096-image batch
-    kernel; 'single' = me_edges on one 32768 x 32768 image (256 MiB).
+    kernel; 'single' = me_edges on one 32768 x 32768 image (256 MiB);
+    'inplace' = me_edges_inplace on that image; 'threshold' =
+    me_threshold_edges on a 16384 x 16384 grey image (256 MiB).
     cfg: optional tile configuration 'engine,rows,vec,threads,ctas,kb,stages[,chunk]'."""
     import torch
     import __graft_entry__
@@ -826,7 +828,7 @@ def run_profile_case(case: str, launches: int, cfg: str | None = None):
             _lib.check(lib.me_edges_batch(descs, len(batch), stream.cuda_stream))
         torch.cuda.synchronize()
         ok, n = verify_sample(batch, dev_out, offs)
-    else:
+    elif case == "single":
         w = h = 32768
         words = synth.bernoulli_half_packed(w, h, seed=0)
         x = torch.from_numpy(words.view(np.int32)).to(device)
@@ -836,13 +838,31 @@ def run_profile_case(case: str, launches: int, cfg: str | None = None):
                                     stream.cuda_stream))
         torch.cuda.synchronize()
         ok = True
+    elif case == "inplace":
+        w = h = 32768
+        words = synth.bernoulli_half_packed(w, h, seed=0)
+        x = torch.from_numpy(words.view(np.int32)).to(device)
+        for _ in range(launches):
+            _lib.check(lib.me_edges_inplace(x.data_ptr(), w, h, 1024, 0, stream.cuda_stream))
+        torch.cuda.synchronize()
+        ok = True
+    else:
+        w = h = 16384
+        g = np.random.default_rng(0)
+        grey = torch.from_numpy(g.integers(0, 256, (h, w), dtype=np.uint8)).to(device)
+        edge = torch.empty((h, w // 32), dtype=torch.int32, device=device)
+        for _ in range(launches):
+            _lib.check(_lib.me_threshold_edges(grey, w, h, w, 128, edge, w // 32, None, 0,
+                                               stream))
+        torch.cuda.synchronize()
+        ok = True
     print(json.dumps({"profile_case": case, "launches": launches, "exact": ok}))
     return 0 if ok else 1
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["batch", "single"], default=None,
+    ap.add_argument("--profile", choices=["batch", "single", "inplace", "threshold"], default=None,
                     help="run a few launches of one kernel for an ncu capture")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--cfg", default=None, help="tile configuration for --profile")
