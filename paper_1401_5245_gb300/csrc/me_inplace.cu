@@ -17,9 +17,9 @@
 //
 // Between CTAs the only shared rows are at the band seams: the last row of
 // a band is the row above the next band, and the first row of a band is the
-// row below the previous one.  A first kernel copies those two rows of
-// every seam into scratch before any band starts, and bands read their
-// outer halo rows from there.
+// row below the previous one.  A first copy saves those two rows of
+// every seam into scratch (one strided copy) before any band starts, and
+// bands read their outer halo rows from there.
 //
 // A band is one row wide in threads and a chain of memory round trips in
 // time, so images of a few bands per SM leave the GPU mostly idle.  Images
@@ -149,9 +149,12 @@ k_inplace(IpGeo g) {
 #pragma unroll
             for (int k = 0; k < C; ++k) {
                 const int v = vcol[k];
+                // the row's own words are fixed (their padding bits reach
+                // pixels through the shifts); above and below, padding bits
+                // meet only output bits that keep clears
                 const uint4 c = fix4(s_ring[s_cur * CT + v], keep[k]);
-                const uint4 u = have_up ? fix4(s_ring[s_up * CT + v], keep[k]) : fill4;
-                const uint4 d = have_dn ? fix4(s_ring[s_dn * CT + v], keep[k]) : fill4;
+                const uint4 u = have_up ? s_ring[s_up * CT + v] : fill4;
+                const uint4 d = have_dn ? s_ring[s_dn * CT + v] : fill4;
                 // the words beside: warp neighbours, the ring at the warp's ends
                 uint32_t lw = __shfl_up_sync(0xFFFFFFFFu, c.w, 1);
                 uint32_t rw = __shfl_down_sync(0xFFFFFFFFu, c.x, 1);
@@ -192,18 +195,6 @@ k_inplace(IpGeo g) {
 template <int C, int Q>
 constexpr size_t inplace_smem(int threads) {
     return (size_t)Q * C * threads * sizeof(uint4);
-}
-
-// Rows on both sides of every seam into scratch: seam k = rows
-// (k+1) * band_rows - 1 and (k+1) * band_rows.
-__global__ void k_inplace_seams(IpGeo g, uint32_t *seam) {
-    const int rows = 2 * (g.nbands - 1);
-    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-        const int y = (r / 2 + 1) * g.band_rows - 1 + (r & 1);
-        const uint32_t *src = g.img + (size_t)y * (size_t)g.stride;
-        uint32_t *dst = seam + (size_t)r * (size_t)g.stride;
-        for (int c = threadIdx.x; c < g.stride; c += blockDim.x) dst[c] = src[c];
-    }
 }
 
 template <int C, bool V16, int Q, int G>
@@ -290,9 +281,13 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
             return record_cuda(e);
         }
         g.seam = seam;
-        const int rows = 2 * (g.nbands - 1);
-        k_inplace_seams<<<std::min(rows, di.sm_count * 8), 256, 0, s>>>(g, seam);
-        e = cudaGetLastError();
+        // rows (k+1) B - 1 and (k+1) B lie next to each other: one strided
+        // copy of nbands - 1 blocks of two rows
+        const size_t row_bytes = (size_t)stride_words * 4;
+        e = cudaMemcpy2DAsync(seam, 2 * row_bytes,
+                              img + (size_t)(g.band_rows - 1) * (size_t)stride_words,
+                              (size_t)g.band_rows * row_bytes, 2 * row_bytes, g.nbands - 1,
+                              cudaMemcpyDeviceToDevice, s);
     }
     if (e == cudaSuccess) {
         // rows of up to 1024 columns: a 12-row ring, 4 rows per barrier;

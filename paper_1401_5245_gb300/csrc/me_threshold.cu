@@ -3,11 +3,12 @@
 // 8-bit image, makes each 32-pixel word on the fly (white where grey >= t),
 // and writes the edge map (and, if asked, the binary image) packed.
 //
-// A warp works on a column block of kWideLanes packed words: lanes 1..30
-// produce those words, lanes 0 and 31 make the words just left and right of
-// the block, so every neighbour word comes from a shuffle.  Each lane walks
-// RPT rows top to bottom; the raw bytes of the next PF rows are already
-// requested, and a row is thresholded only when it is used.
+// A warp works on a tile of kThrRows rows of a column block of kWideLanes
+// packed words: lanes 1..30 produce those words, lanes 0 and 31 make the
+// words just left and right of the block, so every neighbour word comes
+// from a shuffle.  All rows of the tile, with the row above and below, are
+// requested before any is thresholded: one memory round trip per tile, and
+// many tiles in flight per SM.
 #include <algorithm>
 
 #include "me_internal.h"
@@ -16,8 +17,7 @@ namespace me {
 
 namespace {
 
-constexpr int kThrRows = 16;    // rows per warp task
-constexpr int kThrPF = 3;       // rows requested ahead
+constexpr int kThrRows = 4;     // rows per warp task
 
 struct TGeo {
     const uint8_t *grey;
@@ -25,8 +25,7 @@ struct TGeo {
     int32_t w, h, pitch;                // pitch: bytes per grey row
     int32_t stride, nw, ncb;            // output words per row, words with pixels, blocks
     uint32_t lastmask, fill;
-    uint32_t t4;                        // the threshold in every byte
-    int32_t tmode;                      // 0: compare, 1: all white (t <= 0), 2: all black (t > 255)
+    uint32_t t4;                        // 256 - threshold in every byte
 };
 
 struct Raw {
@@ -63,20 +62,35 @@ __device__ __forceinline__ Raw thr_load(const TGeo &g, int y, int wi, bool ok) {
     return r;
 }
 
-// 32 bytes to one word: bit k = byte k >= t.  Per 4 bytes the compare gives
-// 0 or 1 per byte, and the product with 0x01020408 lands byte i's bit at
-// bit 24 + i with every other partial product below bit 24 or above 31.
+// 32 bytes to one word: bit k = byte k >= t, for 1 <= t <= 255.  With
+// c = 256 - t in every byte, a >= t exactly when a + c carries out of the
+// byte's bit 7.  Adding the low 7 bits of a and c never crosses a byte and
+// leaves the carry into bit 7 there; the carry out of bit 7 is the majority
+// of a's bit 7, c's bit 7 and that carry, and c's bit 7 is the same in every
+// byte (C7: t <= 128), so it is (a | s) or (a & s) at bits 7, 15, 23, 31:
+// one three-input logic op per 4 bytes.  The product with 0x00204081 moves
+// those four bits to bits 28..31 (every other partial product falls below
+// bit 28, at distinct positions, or beyond bit 31).
+// MODE: 0 compare with c's bit 7 clear, 1 with it set, 2 all white (t <= 0),
+// 3 all black (t > 255).
+template <int MODE>
 __device__ __forceinline__ uint32_t thr_pack(const TGeo &g, const Raw &r) {
-    if (g.tmode == 1) return kAllOnes;
-    if (g.tmode == 2) return 0u;
+    if constexpr (MODE == 2) return kAllOnes;
+    if constexpr (MODE == 3) return 0u;
     const uint32_t c[8] = {r.a.x, r.a.y, r.a.z, r.a.w, r.b.x, r.b.y, r.b.z, r.b.w};
+    const uint32_t c4_low = g.t4 & 0x7F7F7F7Fu;
     uint32_t out = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) out |= ((__vsetgeu4(c[k], g.t4) * 0x01020408u) >> 24) << (4 * k);
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t s = (c[k] & 0x7F7F7F7Fu) + c4_low;
+        const uint32_t carry = MODE == 1 ? ((c[k] | s) & 0x80808080u) : (c[k] & s & 0x80808080u);
+        // bits 28..31 of the product, placed at bits 4k..4k+3
+        out |= ((carry * 0x00204081u) >> (28 - 4 * k)) & (0xFu << (4 * k));
+    }
     return out;
 }
 
-template <bool V16>
+template <bool V16, int MODE>
 __global__ void __launch_bounds__(256)
 k_threshold(TGeo g, int ntasks) {
     const int lane = threadIdx.x & 31;
@@ -92,33 +106,29 @@ k_threshold(TGeo g, int ntasks) {
         const int y0 = rb * kThrRows;
         auto word = [&](const Raw &r, int y) {
             if ((unsigned)y >= (unsigned)g.h) return g.fill;
-            return (thr_pack(g, r) & keep) | (g.fill & ~keep);
+            return (thr_pack<MODE>(g, r) & keep) | (g.fill & ~keep);
         };
-        uint32_t up = word(thr_load<V16>(g, y0 - 1, wi, loads), y0 - 1);
-        uint32_t cur = word(thr_load<V16>(g, y0, wi, loads), y0);
-        Raw q[kThrPF];
+        // rows y0 - 1 .. y0 + kThrRows, all requested before any is used
+        Raw raw[kThrRows + 2];
 #pragma unroll
-        for (int i = 0; i < kThrPF; ++i) q[i] = thr_load<V16>(g, y0 + 1 + i, wi, loads);
-#pragma unroll 1
-        for (int r0 = 0; r0 < kThrRows; r0 += kThrPF) {
+        for (int i = 0; i < kThrRows + 2; ++i) raw[i] = thr_load<V16>(g, y0 - 1 + i, wi, loads);
+        uint32_t up = word(raw[0], y0 - 1);
+        uint32_t cur = word(raw[1], y0);
 #pragma unroll
-            for (int j = 0; j < kThrPF; ++j) {
-                const int y = y0 + r0 + j;
-                if (r0 + j >= kThrRows) break;
-                const uint32_t dn = word(q[j], y + 1);
-                q[j] = thr_load<V16>(g, y + 1 + kThrPF, wi, loads && r0 + j + 1 + kThrPF <= kThrRows);
-                const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cur, 1);
-                const uint32_t next = __shfl_down_sync(0xFFFFFFFFu, cur, 1);
-                if (writes && y < g.h) {
-                    const uint32_t L = __funnelshift_l(prev, cur, 1);   // I(x-1, y)
-                    const uint32_t R = __funnelshift_r(cur, next, 1);   // I(x+1, y)
-                    const size_t at = (size_t)y * (size_t)g.stride + wi;
-                    __stcs(g.edge + at, ~cur & (L | R | up | dn) & keep);
-                    if (g.binary != nullptr) __stcs(g.binary + at, cur & keep);
-                }
-                up = cur;
-                cur = dn;
+        for (int j = 0; j < kThrRows; ++j) {
+            const int y = y0 + j;
+            const uint32_t dn = word(raw[j + 2], y + 1);
+            const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cur, 1);
+            const uint32_t next = __shfl_down_sync(0xFFFFFFFFu, cur, 1);
+            if (writes && y < g.h) {
+                const uint32_t L = __funnelshift_l(prev, cur, 1);   // I(x-1, y)
+                const uint32_t R = __funnelshift_r(cur, next, 1);   // I(x+1, y)
+                const size_t at = (size_t)y * (size_t)g.stride + wi;
+                __stcs(g.edge + at, ~cur & (L | R | up | dn) & keep);
+                if (g.binary != nullptr) __stcs(g.binary + at, cur & keep);
             }
+            up = cur;
+            cur = dn;
         }
     }
 }
@@ -162,9 +172,9 @@ extern "C" int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int
     g.ncb = (stride_words + kWideLanes - 1) / kWideLanes;
     g.lastmask = (w & 31) ? ((1u << (w & 31)) - 1u) : kAllOnes;
     g.fill = boundary == ME_BOUNDARY_WHITE ? kAllOnes : 0u;
-    const uint32_t t = (uint32_t)std::min(std::max(threshold, 0), 255);
-    g.t4 = t * 0x01010101u;
-    g.tmode = threshold <= 0 ? 1 : (threshold > 255 ? 2 : 0);
+    const uint32_t t = (uint32_t)std::min(std::max(threshold, 1), 255);
+    g.t4 = (256u - t) * 0x01010101u;
+    const int mode = threshold <= 0 ? 2 : threshold > 255 ? 3 : (t <= 128 ? 1 : 0);
 
     const int64_t ntasks = (int64_t)g.ncb * ((h + kThrRows - 1) / kThrRows);
     if (ntasks > INT32_MAX) return ME_ERR_ARG;
@@ -172,10 +182,12 @@ extern "C" int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((ntasks + warps_per_cta - 1) / warps_per_cta,
                                                                  (int64_t)di.sm_count * 64));
     const bool v16 = ((uintptr_t)grey & 15) == 0 && (pitch_bytes & 15) == 0;
-    if (v16)
-        k_threshold<true><<<(unsigned)grid, 32 * warps_per_cta, 0, (cudaStream_t)stream>>>(g, (int)ntasks);
-    else
-        k_threshold<false><<<(unsigned)grid, 32 * warps_per_cta, 0, (cudaStream_t)stream>>>(g, (int)ntasks);
+    using Fn = void (*)(TGeo, int);
+    static constexpr Fn kFns[2][4] = {
+        {k_threshold<false, 0>, k_threshold<false, 1>, k_threshold<false, 2>, k_threshold<false, 3>},
+        {k_threshold<true, 0>, k_threshold<true, 1>, k_threshold<true, 2>, k_threshold<true, 3>}};
+    kFns[v16 ? 1 : 0][mode]<<<(unsigned)grid, 32 * warps_per_cta, 0, (cudaStream_t)stream>>>(
+        g, (int)ntasks);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ME_OK : record_cuda(e);
 }
