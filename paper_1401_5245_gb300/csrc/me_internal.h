@@ -54,6 +54,11 @@ struct BDesc {
     int32_t task_base, ntasks;
 };
 static_assert(sizeof(BDesc) == 64, "BDesc is 64 bytes");
+// the batch kernel reads a descriptor as four 16-byte words in this order
+static_assert(offsetof(BDesc, edge) == 8 && offsetof(BDesc, segs) == 16 &&
+                  offsetof(BDesc, lastmask) == 32 && offsetof(BDesc, vw) == 40 &&
+                  offsetof(BDesc, ncb) == 48 && offsetof(BDesc, task_base) == 56,
+              "BDesc layout");
 
 // Image descriptor of the bulk-copy engine (64 bytes).  The image is cut
 // into bands of band_rows rows x band_words words; a band plus one halo row

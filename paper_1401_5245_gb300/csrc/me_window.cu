@@ -128,27 +128,31 @@ k_batch(const BatchHeader *__restrict__ hdr) {
         }
         for (int t = (int)c0; t < t1; ++t) {
             while (t >= descs[i].task_base + descs[i].ntasks) ++i;
-            const BDesc &d = descs[i];
+            // the 64-byte descriptor as four 128-bit loads
+            const uint4 *dv = reinterpret_cast<const uint4 *>(descs + i);
+            const uint4 d0 = dv[0], d1 = dv[1], d2 = dv[2], d3 = dv[3];
             Geo g;
-            g.img = d.img;
+            g.img = reinterpret_cast<const uint32_t *>(((uint64_t)d0.y << 32) | d0.x);
             g.w = 0;
-            g.h = d.h;
-            g.stride = d.stride;
-            g.nw = d.nw;
-            g.lastmask = d.lastmask;
-            g.fill = d.fill;
-            g.vw = d.vw & 0xff;
-            g.vec16 = d.vw >> 8;
-            g.nv = d.nv;
-            g.seg_w = d.seg_w;
-            g.segs = d.segs;
-            g.ncb = d.ncb;
+            g.segs = (int)d1.x;
+            g.h = (int)d1.y;
+            g.stride = (int)d1.z;
+            g.nw = (int)d1.w;
+            g.lastmask = d2.x;
+            g.fill = d2.y;
+            g.vw = (int)(d2.z & 0xff);
+            g.vec16 = (int)(d2.z >> 8);
+            g.seg_w = (int)d2.w;
+            g.ncb = (int)d3.x;
+            g.nv = (int)d3.y;
             Outs o;
-            o.p[0] = d.edge;
+            o.p[0] = reinterpret_cast<uint32_t *>(((uint64_t)d0.w << 32) | d0.z);
             o.p[1] = o.p[2] = o.p[3] = nullptr;
-            const int local = t - d.task_base;
-            const int cb = local % d.ncb;
-            const int rb = local / d.ncb;
+            const int local = t - (int)d3.z;             // task_base
+            // rows of at most 32 vector columns have one column block: no
+            // division
+            const int cb = g.ncb == 1 ? 0 : local % g.ncb;
+            const int rb = g.ncb == 1 ? local : local / g.ncb;
             if (g.vec16)
                 window_tile<4, RPT, MODE_EDGE, true>(g, o, cb, rb, lane);
             else if constexpr (ANY)
