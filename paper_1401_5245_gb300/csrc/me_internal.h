@@ -38,6 +38,11 @@ struct Geo {
     int32_t seg_w;              // lanes one row segment uses (nv, or 32 when wide)
     int32_t segs;               // row segments stacked in one warp (32 / seg_w)
     int32_t ncb;                // column blocks (kWideLanes columns when nv > 32)
+    // t / ncb for 0 <= t < 2^31 as (t * ncb_m) >> ncb_s (division by an
+    // invariant integer by multiplication, Granlund and Montgomery 1994:
+    // ncb_m = ceil(2^(32+l) / ncb), ncb_s = 32 + l, l = ceil(log2 ncb))
+    uint64_t ncb_m;
+    int32_t ncb_s;
 };
 
 struct Outs {
@@ -165,6 +170,10 @@ inline Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
     g.seg_w = g.nv > 32 ? 32 : g.nv;
     g.segs = kSegs[g.seg_w];
     g.ncb = g.nv > 32 ? (g.nv + kWideLanes - 1) / kWideLanes : 1;
+    int l = 0;
+    while ((1ll << l) < g.ncb) ++l;
+    g.ncb_s = 32 + l;
+    g.ncb_m = (uint64_t)((((unsigned __int128)1 << g.ncb_s) + (unsigned)g.ncb - 1) / (unsigned)g.ncb);
     return g;
 }
 int ceil_log2(int v);

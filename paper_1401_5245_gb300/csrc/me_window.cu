@@ -21,8 +21,8 @@ k_window(Geo g, Outs o, int ntasks) {
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
     for (int t = warp; t < ntasks; t += nwarps) {
-        const int cb = t % g.ncb;
-        const int rb = t / g.ncb;
+        const int rb = (int)(((uint64_t)t * g.ncb_m) >> g.ncb_s);    // t / ncb
+        const int cb = t - rb * g.ncb;
         window_tile<VW, RPT, MODE, V16>(g, o, cb, rb, lane);
     }
 }
