@@ -1,6 +1,6 @@
-"""Host-side logic of the library, tested without a GPU: the range
-allocator the server admits requests with (compiled with g++ from the
-library's own header)."""
+"""Host-side logic of the library, tested without a GPU (compiled with g++
+from the library's own headers): the range allocator the server admits
+requests with, and the image geometry the kernels are launched with."""
 import os
 import subprocess
 
@@ -12,6 +12,19 @@ def test_range_allocator(tmp_path):
     subprocess.check_call(["g++", "-O2", "-std=c++17", "-I",
                            os.path.join(ROOT, "paper_1401_5245_gb300", "csrc"),
                            os.path.join(ROOT, "tests", "host", "test_range_alloc.cpp"),
+                           "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.strip() == "ok"
+
+
+def test_image_geometry(tmp_path):
+    exe = tmp_path / "geometry"
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    subprocess.check_call(["g++", "-O2", "-std=c++17",
+                           "-I", os.path.join(ROOT, "paper_1401_5245_gb300", "csrc"),
+                           "-I", os.path.join(ROOT, "include"), "-I", cuda_inc,
+                           os.path.join(ROOT, "tests", "host", "test_geometry.cpp"),
                            "-o", str(exe)])
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stdout + out.stderr
