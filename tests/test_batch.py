@@ -189,11 +189,13 @@ def test_batch_matches_single_calls():
         assert np.array_equal(aa, rr)
 
 
-def test_full_uneven_batch_4096():
-    """The benchmark's batch: 4096 images, log-uniform 16..4096 per side,
-    glyph strokes, rows padded to 16 bytes; every image against the oracle."""
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_full_uneven_batch_4096(seed):
+    """The benchmark's batch (seed 0) and two more draws of it: 4096 images,
+    log-uniform 16..4096 per side, glyph strokes, rows padded to 16 bytes;
+    every image against the oracle."""
     import torch
-    batch = S.batch(0, workers=8)
+    batch = S.batch(seed, workers=8)
     srcs, dsts, items = [], [], []
     for im in batch:
         x = torch.from_numpy(im.words.view(np.int32)).cuda()
