@@ -533,6 +533,26 @@ def density_leg(lib_mod, stream, reps=64):
             "gpixel_s_l2_resident": round(4096 * 4096 / t_l2 / 1e9, 1)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu or /proc/cpuinfo gives it."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline_leg(batch, budget_s=20.0):
     from oracle import oracle
     from paper_1401_5245_gb300 import synth
@@ -549,7 +569,8 @@ def cpu_baseline_leg(batch, budget_s=20.0):
             break
     return {"value": px / t_used / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} of the {len(batch)} batch images ({px / 1e9:.3f} Gpixel), "
-                      f"single-threaded C oracle, unpack not timed"}
+                      f"single-threaded C oracle, unpack not timed",
+            "cpu_model": cpu_model(), "host_cores": os.cpu_count()}
 
 
 def _oracle_proc(images, barrier, queue):
@@ -590,6 +611,7 @@ def cpu_all_cores_leg(batch):
     px = sum(r[3] for r in res)
     return {"value": round(px / wall / 1e9, 3), "unit": UNIT, "cores": n, "kind": "oracle",
             "sample": f"all {len(batch)} batch images ({px / 1e9:.3f} Gpixel), {n} processes",
+            "cpu_model": cpu_model(),
             "unpack_s_per_gpixel_one_core": round(sum(r[2] for r in res) / (px / 1e9), 3)}
 
 
