@@ -3,12 +3,16 @@
 // 8-bit image, makes each 32-pixel word on the fly (white where grey >= t),
 // and writes the edge map (and, if asked, the binary image) packed.
 //
-// A warp works on a tile of kThrRows rows of a column block of kWideLanes
-// packed words: lanes 1..30 produce those words, lanes 0 and 31 make the
-// words just left and right of the block, so every neighbour word comes
-// from a shuffle.  All rows of the tile, with the row above and below, are
-// requested before any is thresholded: one memory round trip per tile, and
-// many tiles in flight per SM.
+// A warp walks a band of rows of one column block of kWideLanes packed
+// words, top to bottom: lanes 1..30 produce those words, lanes 0 and 31 make
+// the words just left and right of the block, so every neighbour word comes
+// from a shuffle.  Each row of the band (and the one row above and below it)
+// is loaded and thresholded once, and the words of the rows above and at the
+// current row are carried down.  A task starts by requesting its first six
+// rows at once; after that, each row's load is issued as the row four above
+// it is consumed, so four rows per warp stay in flight.  The band height is
+// chosen on the host from the number of resident warps (few waves, little
+// idle tail).
 #include <algorithm>
 
 #include "me_internal.h"
@@ -17,13 +21,15 @@ namespace me {
 
 namespace {
 
-constexpr int kThrRows = 4;     // rows per warp task
+constexpr int kThrRows = 4;     // rows per step of the walk
+constexpr int kThrWarps = 8;    // warps per CTA
 
 struct TGeo {
     const uint8_t *grey;
     uint32_t *edge, *binary;            // binary may be null
     int32_t w, h, pitch;                // pitch: bytes per grey row
     int32_t stride, nw, ncb;            // output words per row, words with pixels, blocks
+    int32_t band;                       // rows per task (a multiple of kThrRows)
     uint32_t lastmask, fill;
     uint32_t t4;                        // 256 - threshold in every byte
 };
@@ -32,28 +38,27 @@ struct Raw {
     uint4 a, b;                         // 32 grey bytes
 };
 
-// The 32 grey bytes of packed word wi of row y (zero where absent).
+// The 32 grey bytes of one packed word from row pointer p (zero where not
+// ok): two 128-bit loads when V16 and the 32 bytes lie inside the row's
+// pitch (vec), else the nb bytes of the row one by one (fully unrolled, so
+// the eight words stay in registers).
 template <bool V16>
-__device__ __forceinline__ Raw thr_load(const TGeo &g, int y, int wi, bool ok) {
+__device__ __forceinline__ Raw thr_load(const uint8_t *p, bool vec, int nb, bool ok) {
     Raw r;
     r.a = make_uint4(0, 0, 0, 0);
     r.b = r.a;
-    if (!ok || (unsigned)y >= (unsigned)g.h) return r;
-    const uint8_t *p = g.grey + (size_t)y * (size_t)g.pitch + (size_t)wi * 32;
-    if (V16 && wi * 32 + 32 <= g.pitch) {
+    if (!ok) return r;
+    if (V16 && vec) {
         r.a = __ldg(reinterpret_cast<const uint4 *>(p));
         r.b = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
     } else {
-        // byte by byte, the bytes of the row only (fully unrolled, so the
-        // eight words stay in registers)
-        const int n = min(32, g.w - wi * 32);
         uint32_t v[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             uint32_t x = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (4 * k + i < n) x |= (uint32_t)__ldg(p + 4 * k + i) << (8 * i);
+                if (4 * k + i < nb) x |= (uint32_t)__ldg(p + 4 * k + i) << (8 * i);
             v[k] = x;
         }
         r.a = make_uint4(v[0], v[1], v[2], v[3]);
@@ -70,67 +75,144 @@ __device__ __forceinline__ Raw thr_load(const TGeo &g, int y, int wi, bool ok) {
 // byte (C7: t <= 128), so it is (a | s) or (a & s) at bits 7, 15, 23, 31:
 // one three-input logic op per 4 bytes.  The product with 0x00204081 moves
 // those four bits to bits 28..31 (every other partial product falls below
-// bit 28, at distinct positions, or beyond bit 31).
+// bit 28, at distinct positions, or beyond bit 31), and a funnel shift
+// appends them below the nibbles already gathered.
 // MODE: 0 compare with c's bit 7 clear, 1 with it set, 2 all white (t <= 0),
 // 3 all black (t > 255).
 template <int MODE>
-__device__ __forceinline__ uint32_t thr_pack(const TGeo &g, const Raw &r) {
+__device__ __forceinline__ uint32_t thr_pack(uint32_t c4_low, const Raw &r) {
     if constexpr (MODE == 2) return kAllOnes;
     if constexpr (MODE == 3) return 0u;
     const uint32_t c[8] = {r.a.x, r.a.y, r.a.z, r.a.w, r.b.x, r.b.y, r.b.z, r.b.w};
-    const uint32_t c4_low = g.t4 & 0x7F7F7F7Fu;
     uint32_t out = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 7; k >= 0; --k) {
         const uint32_t s = (c[k] & 0x7F7F7F7Fu) + c4_low;
         const uint32_t carry = MODE == 1 ? ((c[k] | s) & 0x80808080u) : (c[k] & s & 0x80808080u);
-        // bits 28..31 of the product, placed at bits 4k..4k+3
-        out |= ((carry * 0x00204081u) >> (28 - 4 * k)) & (0xFu << (4 * k));
+        out = __funnelshift_l(carry * 0x00204081u, out, 4);     // (out << 4) | bits 28..31
     }
     return out;
 }
 
+// What a lane needs for one task: its word, its masks, the band's rows.
+struct Lane {
+    int wi, y0, y1;                     // word; rows y0 .. y1-1 are written
+    bool loads, writes;
+    uint32_t keep;
+};
+
+__device__ __forceinline__ Lane thr_lane(const TGeo &g, int t, int lane) {
+    Lane L;
+    const int cb = t % g.ncb;
+    L.y0 = (t / g.ncb) * g.band;
+    L.y1 = min(L.y0 + g.band, g.h);
+    L.wi = cb * kWideLanes + lane - 1;
+    L.loads = L.wi >= 0 && L.wi < g.nw;
+    L.writes = lane >= 1 && lane <= kWideLanes && L.wi < g.stride;
+    L.keep = !L.loads ? 0u : (L.wi < g.nw - 1 ? kAllOnes : g.lastmask);
+    return L;
+}
+
+template <int MODE>
+__device__ __forceinline__ uint32_t thr_word(const TGeo &g, const Lane &L, uint32_t c4_low,
+                                             const Raw &raw, int r) {
+    if ((unsigned)r >= (unsigned)g.h) return g.fill;
+    return (thr_pack<MODE>(c4_low, raw) & L.keep) | (g.fill & ~L.keep);
+}
+
+// The band walk from the words of rows y0 - 1 and y0, over the words that
+// take(r, i) makes for rows r = y0 + 1, y0 + 2, ... in order (i = the row's
+// place in its step, a constant once unrolled): each output row y gets
+// ~I & (L | R | U | D) from the words of rows y - 1, y, y + 1 and its
+// neighbours' words by shuffle.
+template <class Take>
+__device__ __forceinline__ void thr_walk(const TGeo &g, const Lane &L, uint32_t up, uint32_t cur,
+                                         Take &&take) {
+    uint32_t *edge = g.edge + (ptrdiff_t)L.y0 * g.stride + L.wi;
+    uint32_t *bin = g.binary == nullptr ? nullptr : g.binary + (ptrdiff_t)L.y0 * g.stride + L.wi;
+    for (int y = L.y0; y < L.y1; y += kThrRows) {
+        uint32_t dn[kThrRows];
+#pragma unroll
+        for (int i = 0; i < kThrRows; ++i) dn[i] = take(y + 1 + i, i);
+#pragma unroll
+        for (int i = 0; i < kThrRows; ++i) {
+            if (y + i < L.y1) {
+                const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cur, 1);
+                const uint32_t next = __shfl_down_sync(0xFFFFFFFFu, cur, 1);
+                if (L.writes) {
+                    const uint32_t Lw = __funnelshift_l(prev, cur, 1);  // I(x-1, y)
+                    const uint32_t Rw = __funnelshift_r(cur, next, 1);  // I(x+1, y)
+                    __stcs(edge, ~cur & (Lw | Rw | up | dn[i]) & L.keep);
+                    if (bin != nullptr) __stcs(bin, cur & L.keep);
+                }
+                edge += g.stride;
+                if (bin != nullptr) bin += g.stride;
+            }
+            up = cur;
+            cur = dn[i];
+        }
+    }
+}
+
 template <bool V16, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * kThrWarps, 3)
 k_threshold(TGeo g, int ntasks) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
+    const uint32_t c4_low = g.t4 & 0x7F7F7F7Fu;
+    const ptrdiff_t pitch = g.pitch;
     for (int t = warp; t < ntasks; t += nwarps) {
-        const int cb = t % g.ncb;
-        const int rb = t / g.ncb;
-        const int wi = cb * kWideLanes + lane - 1;          // this lane's word
-        const bool loads = wi >= 0 && wi < g.nw;
-        const bool writes = lane >= 1 && lane <= kWideLanes && wi < g.stride;
-        const uint32_t keep = !loads ? 0u : (wi < g.nw - 1 ? kAllOnes : g.lastmask);
-        const int y0 = rb * kThrRows;
-        auto word = [&](const Raw &r, int y) {
-            if ((unsigned)y >= (unsigned)g.h) return g.fill;
-            return (thr_pack<MODE>(g, r) & keep) | (g.fill & ~keep);
+        const Lane L = thr_lane(g, t, lane);
+        const bool vec = (L.wi + 1) * 32 <= g.pitch;
+        const int nb = min(32, g.w - L.wi * 32);
+        // rows y0 - 1 .. y1 are read (y1: the row below the band's last),
+        // one at a time from the top; rp points at the next one's bytes
+        int next = L.y0 - 1;
+        const uint8_t *rp = g.grey + (ptrdiff_t)next * pitch + (ptrdiff_t)L.wi * 32;
+        auto fetch = [&]() {
+            const Raw raw = thr_load<V16>(
+                rp, vec, nb, L.loads && (unsigned)next < (unsigned)g.h && next <= L.y1);
+            ++next;
+            rp += pitch;
+            return raw;
         };
-        // rows y0 - 1 .. y0 + kThrRows, all requested before any is used
-        Raw raw[kThrRows + 2];
+        const Raw r_up = fetch();
+        const Raw r_cur = fetch();
+        Raw ahead[kThrRows];
 #pragma unroll
-        for (int i = 0; i < kThrRows + 2; ++i) raw[i] = thr_load<V16>(g, y0 - 1 + i, wi, loads);
-        uint32_t up = word(raw[0], y0 - 1);
-        uint32_t cur = word(raw[1], y0);
-#pragma unroll
-        for (int j = 0; j < kThrRows; ++j) {
-            const int y = y0 + j;
-            const uint32_t dn = word(raw[j + 2], y + 1);
-            const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, cur, 1);
-            const uint32_t next = __shfl_down_sync(0xFFFFFFFFu, cur, 1);
-            if (writes && y < g.h) {
-                const uint32_t L = __funnelshift_l(prev, cur, 1);   // I(x-1, y)
-                const uint32_t R = __funnelshift_r(cur, next, 1);   // I(x+1, y)
-                const size_t at = (size_t)y * (size_t)g.stride + wi;
-                __stcs(g.edge + at, ~cur & (L | R | up | dn) & keep);
-                if (g.binary != nullptr) __stcs(g.binary + at, cur & keep);
-            }
-            up = cur;
-            cur = dn;
+        for (int i = 0; i < kThrRows; ++i) ahead[i] = fetch();
+        auto take = [&](int r, int i) {
+            const uint32_t w = thr_word<MODE>(g, L, c4_low, ahead[i], r);
+            ahead[i] = fetch();                             // row r + kThrRows
+            return w;
+        };
+        thr_walk(g, L, thr_word<MODE>(g, L, c4_low, r_up, L.y0 - 1),
+                 thr_word<MODE>(g, L, c4_low, r_cur, L.y0), take);
+    }
+}
+
+// Rows per band: the multiple of kThrRows that minimises the walk's length,
+// counted in rows per warp: the waves of tasks over the resident warps times
+// the rows one task reads (band + 2) plus about four rows' worth of set-up.
+// For k waves the shortest band that fits is found directly, for k up to 64.
+int pick_band(int64_t ncb, int32_t h, int64_t resident_warps) {
+    const int64_t min_band_waves = (ncb * (((int64_t)h + kThrRows - 1) / kThrRows) +
+                                    resident_warps - 1) / resident_warps;
+    int best = kThrRows;
+    int64_t best_cost = INT64_MAX;
+    for (int64_t k = 1; k <= std::min<int64_t>(min_band_waves, 64); ++k) {
+        const int64_t bands = std::max<int64_t>(1, k * resident_warps / ncb);   // per column
+        int64_t band = ((int64_t)h + bands - 1) / bands;
+        band = std::max<int64_t>(kThrRows, (band + kThrRows - 1) / kThrRows * kThrRows);
+        const int64_t tasks = ncb * (((int64_t)h + band - 1) / band);
+        const int64_t cost = (tasks + resident_warps - 1) / resident_warps * (band + 2 + 4);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = (int)std::min<int64_t>(band, INT32_MAX);
         }
     }
+    return best;
 }
 
 }  // namespace
@@ -176,18 +258,22 @@ extern "C" int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int
     g.t4 = (256u - t) * 0x01010101u;
     const int mode = threshold <= 0 ? 2 : threshold > 255 ? 3 : (t <= 128 ? 1 : 0);
 
-    const int64_t ntasks = (int64_t)g.ncb * ((h + kThrRows - 1) / kThrRows);
-    if (ntasks > INT32_MAX) return ME_ERR_ARG;
-    const int warps_per_cta = 8;
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((ntasks + warps_per_cta - 1) / warps_per_cta,
-                                                                 (int64_t)di.sm_count * 64));
     const bool v16 = ((uintptr_t)grey & 15) == 0 && (pitch_bytes & 15) == 0;
     using Fn = void (*)(TGeo, int);
     static constexpr Fn kFns[2][4] = {
         {k_threshold<false, 0>, k_threshold<false, 1>, k_threshold<false, 2>, k_threshold<false, 3>},
         {k_threshold<true, 0>, k_threshold<true, 1>, k_threshold<true, 2>, k_threshold<true, 3>}};
-    kFns[v16 ? 1 : 0][mode]<<<(unsigned)grid, 32 * warps_per_cta, 0, (cudaStream_t)stream>>>(
-        g, (int)ntasks);
+    const Fn fn = kFns[v16 ? 1 : 0][mode];
+    int occ = 0;
+    if ((rc = cached_occupancy(reinterpret_cast<const void *>(fn), 32 * kThrWarps, 0, &occ)) != ME_OK)
+        return rc;
+    const int64_t resident = (int64_t)std::max(1, occ) * di.sm_count * kThrWarps;
+    g.band = pick_band(g.ncb, h, resident);
+    const int64_t ntasks = (int64_t)g.ncb * ((h + g.band - 1) / g.band);
+    if (ntasks > INT32_MAX) return ME_ERR_ARG;
+    const int64_t grid = std::max<int64_t>(
+        1, (std::min(ntasks, resident) + kThrWarps - 1) / kThrWarps);
+    fn<<<(unsigned)grid, 32 * kThrWarps, 0, (cudaStream_t)stream>>>(g, (int)ntasks);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ME_OK : record_cuda(e);
 }

@@ -80,6 +80,16 @@ def test_unaligned_grey_start():
     run(grey, 128, 1, 512, S.batch_stride(500), True, grey_off=3)
 
 
+@pytest.mark.parametrize("pitch", [2000, 2003])
+def test_tall_image_long_bands(pitch):
+    """A tall image in few column blocks: each warp walks a band of many rows
+    (rows pass through the row ring several times; the last band is partly
+    filled), on the 16-byte path (pitch 2000) and the byte path (2003).
+    Every row is compared."""
+    grey = np.tile(grey_image(2000, 667, 11), (30, 1))[:20001]
+    run(grey, 128, 1, pitch, S.batch_stride(2000), True)
+
+
 def test_large_image_sampled_rows():
     """8192 x 8192 (64 MiB of grey): whole rows compared at the top, the
     bottom and every 512th row in between."""
