@@ -17,9 +17,9 @@
 //
 // Between CTAs the only shared rows are at the band seams: the last row of
 // a band is the row above the next band, and the first row of a band is the
-// row below the previous one.  A first copy saves those two rows of
-// every seam into scratch (one strided copy) before any band starts, and
-// bands read their outer halo rows from there.
+// row below the previous one.  A first small kernel saves those two rows
+// of every seam into scratch before any band starts, and bands read their
+// outer halo rows from there.
 //
 // A band is one row wide in threads and a chain of memory round trips in
 // time, so images of a few bands per SM leave the GPU mostly idle.  Images
@@ -192,6 +192,24 @@ k_inplace(IpGeo g) {
     cp_async_wait<0>();
 }
 
+// The seam rows into scratch before any band starts: CTA k copies rows
+// (k+1) B - 1 and (k+1) B, which lie next to each other, as one run of
+// 2 * stride words (16-byte units when the rows allow them).
+template <bool V16>
+__global__ void __launch_bounds__(256)
+k_seams(const uint32_t *img, uint32_t *seam, int32_t stride, int32_t band_rows) {
+    const size_t words = 2 * (size_t)stride;
+    const uint32_t *src = img + ((size_t)(blockIdx.x + 1) * band_rows - 1) * (size_t)stride;
+    uint32_t *dst = seam + (size_t)blockIdx.x * words;
+    if constexpr (V16) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (size_t i = threadIdx.x; i < words / 4; i += blockDim.x) d4[i] = s4[i];
+    } else {
+        for (size_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
 template <int C, int Q>
 constexpr size_t inplace_smem(int threads) {
     return (size_t)Q * C * threads * sizeof(uint4);
@@ -281,13 +299,11 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
             return record_cuda(e);
         }
         g.seam = seam;
-        // rows (k+1) B - 1 and (k+1) B lie next to each other: one strided
-        // copy of nbands - 1 blocks of two rows
-        const size_t row_bytes = (size_t)stride_words * 4;
-        e = cudaMemcpy2DAsync(seam, 2 * row_bytes,
-                              img + (size_t)(g.band_rows - 1) * (size_t)stride_words,
-                              (size_t)g.band_rows * row_bytes, 2 * row_bytes, g.nbands - 1,
-                              cudaMemcpyDeviceToDevice, s);
+        if (geo.vec16)
+            k_seams<true><<<g.nbands - 1, 256, 0, s>>>(img, seam, stride_words, g.band_rows);
+        else
+            k_seams<false><<<g.nbands - 1, 256, 0, s>>>(img, seam, stride_words, g.band_rows);
+        e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         // rows of up to 1024 columns: a 12-row ring, 4 rows per barrier;
