@@ -344,13 +344,14 @@ def c1_leg(lib_mod, stream, seeds=(0, 1, 2), reps=2000):
                 v["us_per_call_back_to_back"] for v in out.values()) / 1e3, 2)}
 
 
-def threshold_leg(lib_mod, stream, peak):
-    """Section 7's front end fused with the method: an 8192 x 8192 grey image
-    (64 MiB, 8 bits per pixel) thresholded at 128 and its edges found in one
-    pass, with and without the packed binary image; 3 rotating inputs."""
+def threshold_leg(lib_mod, stream, peak, side=8192):
+    """Section 7's front end fused with the method: a side x side grey image
+    (8 bits per pixel: 64 MiB at 8192, 256 MiB at 16384) thresholded at 128
+    and its edges found in one pass, with and without the binary image;
+    3 rotating inputs."""
     import torch
     from oracle import oracle
-    w = h = 8192
+    w = h = side
     g = np.random.default_rng(0)
     yy, xx = np.mgrid[0:256, 0:w]
     tile = np.clip((np.sin(xx / 7.0) + np.cos(yy / 11.0)) * 60 + 128 + g.normal(0, 25, (256, w)),
@@ -380,6 +381,7 @@ def threshold_leg(lib_mod, stream, peak):
         out[name] = {"us": round(t * 1e6, 2), "gpixel_s": round(w * h / t / 1e9, 1),
                      "gb_s": round(nbytes / t / 1e9, 1),
                      "frac_of_peak": round(nbytes / t / 1e9 / peak, 4)}
+    del xs
     return out
 
 
@@ -792,6 +794,7 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.quick:
         extra["threshold_8192"] = threshold_leg(_lib, stream, peak)
+        extra["threshold_16384"] = threshold_leg(_lib, stream, peak, 16384)
         extra["c1_256"] = c1_leg(_lib, stream)
         extra["data_independence_4096"] = density_leg(_lib, stream)
         extra["unpadded_batch"] = unpadded_leg(_lib, stream, peak)
