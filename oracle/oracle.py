@@ -144,6 +144,41 @@ def threshold(grey, t: int) -> np.ndarray:
     return out
 
 
+def otsu_threshold(grey) -> int:
+    """Otsu's rule for the threshold of Section 7's grey photograph (the paper
+    names none; N. Otsu, "A threshold selection method from gray-level
+    histograms", IEEE Trans. SMC 9(1), 1979): the t in 1..255 whose classes
+    grey < t and grey >= t have the largest between-class variance
+    w0 w1 (mu1 - mu0)^2.  With N pixels, S the sum of all grey values, n0
+    pixels and s0 grey sum below t, that variance is
+    (S n0 - s0 N)^2 / (N^2 n0 (N - n0)); N^2 is common to every t, so
+    D(t) = x^2 / (n0 (N - n0)), x = S n0 - s0 N, is compared, for t with
+    0 < n0 < N.  The comparison is taken in IEEE double arithmetic in exactly
+    this order (x = S*n0 - s0*N, then x*x / (n0 * (N - n0)), every operand an
+    exact integer converted to double), the first largest t wins, and an
+    image of one grey value v takes t = v (every pixel white)."""
+    a = np.asarray(grey, dtype=np.uint8)
+    if a.size == 0:
+        raise ValueError("empty image")
+    hist = np.bincount(a.ravel(), minlength=256)
+    N = int(a.size)
+    S = sum(i * int(hist[i]) for i in range(256))
+    best_t, best_d = None, None
+    n0 = s0 = 0
+    for t in range(1, 256):
+        n0 += int(hist[t - 1])
+        s0 += (t - 1) * int(hist[t - 1])
+        if n0 == 0 or n0 == N:
+            continue
+        x = float(S) * float(n0) - float(s0) * float(N)
+        d = (x * x) / (float(n0) * float(N - n0))
+        if best_d is None or d > best_d:
+            best_t, best_d = t, d
+    if best_t is None:
+        return int(a.flat[0])
+    return best_t
+
+
 # ----------------------------------------------------------------------------
 # brute force over the full definition of Section 1
 # ----------------------------------------------------------------------------

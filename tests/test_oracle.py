@@ -6,6 +6,8 @@
 * hand-built cases and invariants (edge = black AND NOT erode4(black) with
   scipy's binary erosion, flips, transposes, all-white, all-black);
 * the end-point map (second clause) against a scipy neighbour count;
+* Otsu's threshold: a closed form for two grey levels, constant images, the
+  within-class form computed from the class pixels, shift and inversion;
 * planted mistakes in a copy of the C source must fail at least one pin.
 """
 import ctypes
@@ -285,6 +287,101 @@ def test_threshold_counts_match_the_histogram(seed):
         if prev is not None:
             assert not (b & (1 - prev)).any()
         prev = b
+
+
+# ---------------------------------------------------------------------------
+# Otsu's threshold for Section 7's photograph (the paper names no rule)
+# ---------------------------------------------------------------------------
+
+def mixture(seed, h, w, mus, sigmas, weights):
+    """Grey pixels drawn from a mixture of clipped normals."""
+    g = np.random.default_rng(seed)
+    k = g.choice(len(mus), size=(h, w), p=weights)
+    v = g.normal(np.asarray(mus)[k], np.asarray(sigmas)[k])
+    return np.clip(np.rint(v), 0, 255).astype(np.uint8)
+
+
+def within_class_argmin(grey):
+    """Otsu's criterion in its other form, from the pixels themselves: the t
+    in 1..255 with the least within-class variance w0 var0 + w1 var1 of the
+    classes grey < t and grey >= t (Otsu 1979: within- plus between-class
+    variance is the total variance, so the least of one is the largest of
+    the other), each class's variance by numpy's var on its pixels.  Returns
+    t and the relative margin to the best t with another split."""
+    v = grey.ravel().astype(np.float64)
+    best = {}
+    for t in range(1, 256):
+        lo, hi = v[v < t], v[v >= t]
+        if lo.size == 0 or hi.size == 0:
+            continue
+        score = (lo.size * lo.var() + hi.size * hi.var()) / v.size
+        key = lo.size                       # thresholds with the same split tie
+        if key not in best or score < best[key][0]:
+            best[key] = (score, t)
+    ranked = sorted(best.values())
+    (s1, t1), (s2, _) = ranked[0], ranked[1]
+    return t1, (s2 - s1) / max(s1, 1e-300)
+
+
+MIXTURES = [
+    (0, 48, 64, (60, 180), (15, 20), (0.5, 0.5)),
+    (1, 40, 70, (40, 140), (10, 30), (0.7, 0.3)),
+    (2, 64, 64, (100, 130, 220), (12, 8, 10), (0.4, 0.3, 0.3)),
+    (3, 33, 97, (20, 235), (5, 5), (0.9, 0.1)),
+    (4, 50, 50, (128,), (40,), (1.0,)),
+]
+
+
+def otsu_pins(otsu):
+    """Every check that pins an Otsu threshold function."""
+    # two grey levels a < b: every t in a+1..b makes the same two classes,
+    # and the first of the tied t wins
+    for a, b, na, nb in ((50, 200, 10, 30), (0, 255, 1, 1), (7, 8, 5, 100), (100, 101, 3, 2)):
+        grey = np.array([[a] * na + [b] * nb], dtype=np.uint8)
+        assert otsu(grey) == a + 1, (a, b, na, nb)
+    # one grey value: every pixel white
+    for v in (0, 1, 77, 255):
+        assert otsu(np.full((3, 5), v, dtype=np.uint8)) == v
+    # the within-class form, computed from the class pixels
+    for seed, h, w, mus, sig, wts in MIXTURES:
+        grey = mixture(seed, h, w, mus, sig, wts)
+        t_ref, gap = within_class_argmin(grey)
+        assert gap > 1e-9, "ambiguous case"
+        assert otsu(grey) == t_ref, (seed, otsu(grey), t_ref)
+    # shifting every grey value by c shifts t by c; inverting the grey
+    # scale (255 - grey) swaps the two classes, so the split is the same
+    # (t itself may move within a run of empty bins: the first t wins)
+    for seed, h, w, mus, sig, wts in MIXTURES[:3]:
+        grey = np.clip(mixture(seed, h, w, mus, sig, wts), 10, 200)
+        t = otsu(grey)
+        assert otsu(grey + 40) == t + 40
+        inv = 255 - grey
+        assert np.array_equal(grey >= t, inv < otsu(inv))
+
+
+def test_otsu_pins():
+    otsu_pins(O.otsu_threshold)
+
+
+OTSU_MUTATIONS = {
+    "grey sum off by one": ("s0 += (t - 1) * int(hist[t - 1])", "s0 += t * int(hist[t - 1])"),
+    "one class size": ("(float(n0) * float(N - n0))", "(float(n0) * float(N))"),
+    "square dropped": ("d = (x * x) /", "d = abs(x) /"),
+    "last tie wins": ("d > best_d", "d >= best_d"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(OTSU_MUTATIONS))
+def test_otsu_planted_mistake_is_caught(name):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(O.otsu_threshold))
+    old, new = OTSU_MUTATIONS[name]
+    assert old in src
+    ns = {"np": np}
+    exec(src.replace(old, new), ns)
+    with pytest.raises(AssertionError):
+        otsu_pins(ns["otsu_threshold"])
 
 
 # ---------------------------------------------------------------------------
