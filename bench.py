@@ -385,6 +385,49 @@ def threshold_leg(lib_mod, stream, peak, side=8192):
     return out
 
 
+def otsu_leg(lib_mod, stream, peak, side=16384):
+    """The front end with Otsu's threshold chosen on the device
+    (me_threshold_edges_otsu): a side x side photo-like grey image (two
+    clipped normal modes); the histogram pass reads the grey image, the edge
+    pass reads it again and writes the edge map (2 x 8 + 1 bits per pixel).
+    The threshold is checked against the oracle's on the whole image and
+    the first 299 edge rows bit by bit; 3 rotating inputs."""
+    import torch
+    from oracle import oracle
+    from paper_1401_5245_gb300 import synth
+    w = h = side
+    g = np.random.default_rng(3)
+    k = g.random((512, w)) < 0.6
+    tile = np.clip(np.rint(np.where(k, g.normal(70, 18, (512, w)), g.normal(185, 22, (512, w)))),
+                   0, 255).astype(np.uint8)
+    grey = np.tile(tile, (h // 512, 1))
+    xs = [torch.from_numpy(grey).cuda() for _ in range(3)]
+    edge = torch.empty((h, w // 32), dtype=torch.int32, device="cuda")
+    tdev = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lib_mod.check(lib_mod.me_threshold_edges_otsu(xs[0], w, h, w, edge, w // 32, None, 0, tdev,
+                                                  stream))
+    torch.cuda.synchronize()
+    t_ref = oracle.otsu_threshold(grey)
+    t_got = int(tdev.item())
+    want = oracle.edges(oracle.threshold(grey[:300], t_ref), 0)
+    got = synth.unpack(edge[:299].cpu().numpy().view(np.uint32), w)
+    exact = bool(t_got == t_ref and np.array_equal(got, want[:299]))
+    c = [0]
+
+    def one():
+        i = c[0] % 3
+        c[0] += 1
+        lib_mod.check(lib_mod.me_threshold_edges_otsu(xs[i], w, h, w, edge, w // 32, None, 0,
+                                                      tdev, stream))
+    one()
+    t = time_events(one, 30, stream)
+    nbytes = 2 * w * h + w * h // 8
+    del xs
+    return {"threshold": t_got, "exact_threshold_and_first_299_rows": exact,
+            "us": round(t * 1e6, 2), "gpixel_s": round(w * h / t / 1e9, 1),
+            "gb_s": round(nbytes / t / 1e9, 1), "frac_of_peak": round(nbytes / t / 1e9 / peak, 4)}
+
+
 def unpadded_leg(lib_mod, stream, peak):
     """The uneven batch with stride = ceil(w / 32) (no padding to 16 bytes):
     rows are not 16-byte groups, so every image takes the 32-bit path."""
@@ -795,6 +838,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.quick:
         extra["threshold_8192"] = threshold_leg(_lib, stream, peak)
         extra["threshold_16384"] = threshold_leg(_lib, stream, peak, 16384)
+        extra["threshold_otsu_16384"] = otsu_leg(_lib, stream, peak)
         extra["c1_256"] = c1_leg(_lib, stream)
         extra["data_independence_4096"] = density_leg(_lib, stream)
         extra["unpadded_batch"] = unpadded_leg(_lib, stream, peak)

@@ -223,6 +223,30 @@ int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int32_t pitch_
                        int32_t threshold, uint32_t *edge, int32_t stride_words,
                        uint32_t *binary, int32_t boundary, me_stream_t stream);
 
+/*
+ * As me_threshold_edges with the threshold chosen from the image by Otsu's
+ * rule (N. Otsu, IEEE Trans. SMC 9(1), 1979; Section 7 names no rule): the
+ * t in 1..255 whose classes grey < t and grey >= t have the largest
+ * between-class variance, scored as D(t) = x^2 / (n0 (N - n0)) with
+ * x = S n0 - s0 N (N pixels, S their grey sum, n0 and s0 the same below t),
+ * each operation a correctly rounded double operation in that order; the
+ * first largest t wins, and an image of one grey value v takes t = v (all
+ * white).  Three kernels on the stream: the grey histogram (8 bits read per
+ * pixel), the choice of t (one CTA), then the one-pass threshold and edge
+ * kernel reading t from device memory.  Asynchronous: t is not returned to
+ * the host.
+ *
+ * grey, w, h, pitch_bytes, edge, stride_words, binary, boundary, stream
+ *               as me_threshold_edges.
+ * threshold_out NULL, or a 4-byte aligned device int32 that receives t.
+ * Scratch of about 2 KB comes from the stream-ordered allocator; failure to
+ * get it returns ME_ERR_CUDA with nothing enqueued.  threshold_out must not
+ * overlap grey, edge or binary (ME_ERR_ALIAS).
+ */
+int me_threshold_edges_otsu(const uint8_t *grey, int32_t w, int32_t h, int32_t pitch_bytes,
+                            uint32_t *edge, int32_t stride_words, uint32_t *binary,
+                            int32_t boundary, int32_t *threshold_out, me_stream_t stream);
+
 /* ---- many images in one launch ----------------------------------------- */
 
 typedef struct me_desc {

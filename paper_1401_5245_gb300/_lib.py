@@ -93,6 +93,8 @@ PROTOTYPES = {
     "me_edges_inplace": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_i32, c_vp]),
     "me_threshold_edges": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_i32, c_vp, c_i32,
                                           c_vp, c_i32, c_vp]),
+    "me_threshold_edges_otsu": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_vp, c_i32, c_vp,
+                                               c_i32, c_vp, c_vp]),
     "me_edges_batch": (ctypes.c_int, [ctypes.POINTER(me_desc), c_i32, c_vp]),
     "me_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(me_desc), c_i32, c_vp,
                                             ctypes.POINTER(c_vp)]),
@@ -187,6 +189,13 @@ def me_threshold_edges(grey, w, h, pitch_bytes, threshold, edge, stride_words, b
                        boundary=0, stream=None) -> int:
     return load().me_threshold_edges(ptr(grey), w, h, pitch_bytes, threshold, ptr(edge),
                                      stride_words, ptr(binary), boundary, stream_handle(stream))
+
+
+def me_threshold_edges_otsu(grey, w, h, pitch_bytes, edge, stride_words, binary=None,
+                            boundary=0, threshold_out=None, stream=None) -> int:
+    return load().me_threshold_edges_otsu(ptr(grey), w, h, pitch_bytes, ptr(edge), stride_words,
+                                          ptr(binary), boundary, ptr(threshold_out),
+                                          stream_handle(stream))
 
 
 def me_edges_staged_static(img, w, h, stride_words, edge, boundary=0, stream=None) -> int:

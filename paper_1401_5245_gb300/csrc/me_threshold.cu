@@ -155,8 +155,7 @@ __device__ __forceinline__ void thr_walk(const TGeo &g, const Lane &L, uint32_t 
 }
 
 template <bool V16, int MODE>
-__global__ void __launch_bounds__(32 * kThrWarps, 3)
-k_threshold(TGeo g, int ntasks) {
+__device__ __forceinline__ void thr_run(const TGeo &g, int ntasks) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
@@ -192,6 +191,148 @@ k_threshold(TGeo g, int ntasks) {
     }
 }
 
+template <bool V16, int MODE>
+__global__ void __launch_bounds__(32 * kThrWarps, 3)
+k_threshold(TGeo g, int ntasks) {
+    thr_run<V16, MODE>(g, ntasks);
+}
+
+// The same with the threshold read from device memory (written there by
+// k_otsu earlier on the stream): the compare form is chosen per launch.
+template <bool V16>
+__global__ void __launch_bounds__(32 * kThrWarps, 3)
+k_threshold_dev(TGeo g, int ntasks, const int32_t *__restrict__ t_dev) {
+    const int t = *t_dev;
+    const uint32_t tc = (uint32_t)min(max(t, 1), 255);
+    g.t4 = (256u - tc) * 0x01010101u;
+    if (t <= 0)
+        thr_run<V16, 2>(g, ntasks);
+    else if (t > 255)
+        thr_run<V16, 3>(g, ntasks);
+    else if (t <= 128)
+        thr_run<V16, 1>(g, ntasks);
+    else
+        thr_run<V16, 0>(g, ntasks);
+}
+
+// ---- Otsu's threshold (N. Otsu, IEEE Trans. SMC 9(1), 1979) ----
+
+constexpr int kHistWarps = 8;
+constexpr int kHistGroups = 4;  // 16-byte groups per lane in flight
+
+// The grey histogram: one warp per row (rows strided over the grid), lanes
+// over 16-byte groups of the row (bytes one by one otherwise), counts in a
+// histogram per warp in shared memory, added into hist (256 counters) at
+// the end.  Only the w pixels of a row count, not its padding.  Shared
+// atomics bound it: about nine updates of distinct counters per clock per
+// SM, i.e. about 2.7 TB/s of grey on varied images (updates of one counter
+// within a warp merge, so a flat image reads at the copy rate).  A counter
+// column per lane (no bank conflicts at all) and plain read-modify-write
+// in such columns both measured slower.
+template <bool V16>
+__global__ void __launch_bounds__(32 * kHistWarps)
+k_grey_hist(const uint8_t *__restrict__ grey, int32_t w, int32_t h, int32_t pitch,
+            unsigned long long *__restrict__ hist) {
+    __shared__ uint32_t sh[kHistWarps][256];
+    for (int i = threadIdx.x; i < kHistWarps * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    uint32_t *mine = sh[threadIdx.x >> 5];
+    const int nwarps = gridDim.x * kHistWarps;
+    for (int y = blockIdx.x * kHistWarps + (threadIdx.x >> 5); y < h; y += nwarps) {
+        const uint8_t *row = grey + (size_t)y * (size_t)pitch;
+        if constexpr (V16) {
+            // four 16-byte groups per lane requested before any is counted
+            for (int x0 = lane * 16; x0 < w; x0 += kHistGroups * 32 * 16) {
+                uint4 v[kHistGroups];
+#pragma unroll
+                for (int j = 0; j < kHistGroups; ++j) {
+                    const int x = x0 + j * 32 * 16;
+                    v[j] = x < w ? __ldcs(reinterpret_cast<const uint4 *>(row + x))
+                                 : make_uint4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int j = 0; j < kHistGroups; ++j) {
+                    const int x = x0 + j * 32 * 16;
+                    const uint32_t b[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+                    if (x + 16 <= w) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            atomicAdd(&mine[(b[k >> 2] >> (8 * (k & 3))) & 0xFF], 1u);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            if (x + k < w) atomicAdd(&mine[(b[k >> 2] >> (8 * (k & 3))) & 0xFF], 1u);
+                    }
+                }
+            }
+        } else {
+            for (int x = lane; x < w; x += 32) atomicAdd(&mine[row[x]], 1u);
+        }
+    }
+    __syncthreads();
+    for (int bin = threadIdx.x; bin < 256; bin += blockDim.x) {
+        unsigned long long c = 0;
+#pragma unroll
+        for (int k = 0; k < kHistWarps; ++k) c += sh[k][bin];
+        if (c != 0) atomicAdd(&hist[bin], c);
+    }
+}
+
+// The threshold from the histogram, by one CTA of 256 threads: thread i
+// takes t = i + 1 (1..255).  With n0, s0 the pixels and grey sum below t
+// (prefix sums of the histogram), N and S their totals, t is scored by
+// D(t) = x^2 / (n0 (N - n0)), x = S n0 - s0 N: the between-class variance
+// times N^2.  Every operation is an explicitly rounded double operation in
+// that order (no fused multiply-add), so the scores and their comparison
+// are those of the same formula evaluated in IEEE double arithmetic
+// anywhere.  The first largest t wins; with one grey value v, t = v.
+__global__ void __launch_bounds__(256)
+k_otsu(const unsigned long long *__restrict__ hist, int32_t *__restrict__ t_out) {
+    __shared__ unsigned long long n_s[256], s_s[256];
+    __shared__ double best_d[256];
+    __shared__ int best_t[256];
+    __shared__ int single;
+    const int i = threadIdx.x;
+    const unsigned long long c = hist[i];
+    n_s[i] = c;
+    s_s[i] = c * (unsigned long long)i;
+    if (i == 0) single = -1;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {               // inclusive prefix sums
+        const unsigned long long a = i >= off ? n_s[i - off] : 0;
+        const unsigned long long b = i >= off ? s_s[i - off] : 0;
+        __syncthreads();
+        n_s[i] += a;
+        s_s[i] += b;
+        __syncthreads();
+    }
+    const unsigned long long N = n_s[255], S = s_s[255];
+    if (c == N) single = i;                                 // one grey value (N > 0)
+    const unsigned long long n0 = n_s[i], s0 = s_s[i];      // below t = i + 1
+    double d = -1.0;
+    if (i < 255 && n0 > 0 && n0 < N) {
+        const double x = __dsub_rn(__dmul_rn(__ull2double_rn(S), __ull2double_rn(n0)),
+                                   __dmul_rn(__ull2double_rn(s0), __ull2double_rn(N)));
+        d = __ddiv_rn(__dmul_rn(x, x), __dmul_rn(__ull2double_rn(n0), __ull2double_rn(N - n0)));
+    }
+    best_d[i] = d;
+    best_t[i] = i + 1;
+    __syncthreads();
+    for (int half = 128; half > 0; half >>= 1) {            // first largest
+        if (i < half) {
+            const double od = best_d[i + half];
+            const int ot = best_t[i + half];
+            if (od > best_d[i] || (od == best_d[i] && ot < best_t[i])) {
+                best_d[i] = od;
+                best_t[i] = ot;
+            }
+        }
+        __syncthreads();
+    }
+    if (i == 0) *t_out = best_d[0] < 0.0 ? single : best_t[0];
+}
+
 // Rows per band: the multiple of kThrRows that minimises the walk's length,
 // counted in rows per warp: the waves of tasks over the resident warps times
 // the rows one task reads (band + 2) plus about four rows' worth of set-up.
@@ -221,9 +362,13 @@ int pick_band(int64_t ncb, int32_t h, int64_t resident_warps) {
 
 using namespace me;
 
-extern "C" int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int32_t pitch_bytes,
-                                  int32_t threshold, uint32_t *edge, int32_t stride_words,
-                                  uint32_t *binary, int32_t boundary, me_stream_t stream) {
+namespace me {
+namespace {
+
+// Argument checks and the geometry shared by both entry points (t4 and the
+// band are filled in later).
+int thr_setup(const uint8_t *grey, int32_t w, int32_t h, int32_t pitch_bytes, uint32_t *edge,
+              int32_t stride_words, uint32_t *binary, int32_t boundary, TGeo *g, bool *v16) {
     if (grey == nullptr || edge == nullptr || w <= 0 || h <= 0 || pitch_bytes < w ||
         stride_words < (int32_t)(((int64_t)w + 31) / 32) ||
         (boundary != ME_BOUNDARY_WHITE && boundary != ME_BOUNDARY_BLACK) ||
@@ -239,41 +384,116 @@ extern "C" int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int
     if (rc == ME_OK) rc = check_device_ptr(edge);
     if (rc == ME_OK && binary != nullptr) rc = check_device_ptr(binary);
     if (rc != ME_OK) return rc;
-    DevInfo di;
-    if ((rc = device_info(&di)) != ME_OK) return rc;
+    g->grey = grey;
+    g->edge = edge;
+    g->binary = binary;
+    g->w = w;
+    g->h = h;
+    g->pitch = pitch_bytes;
+    g->stride = stride_words;
+    g->nw = (int32_t)(((int64_t)w + 31) / 32);
+    g->ncb = (stride_words + kWideLanes - 1) / kWideLanes;
+    g->lastmask = (w & 31) ? ((1u << (w & 31)) - 1u) : kAllOnes;
+    g->fill = boundary == ME_BOUNDARY_WHITE ? kAllOnes : 0u;
+    g->t4 = 0;
+    g->band = kThrRows;
+    *v16 = ((uintptr_t)grey & 15) == 0 && (pitch_bytes & 15) == 0;
+    return ME_OK;
+}
 
+// Band height, task count and grid for kernel fn on this device.
+int thr_grid(const void *fn, TGeo *g, int *ntasks, unsigned *grid) {
+    DevInfo di;
+    int rc = device_info(&di);
+    if (rc != ME_OK) return rc;
+    int occ = 0;
+    if ((rc = cached_occupancy(fn, 32 * kThrWarps, 0, &occ)) != ME_OK) return rc;
+    const int64_t resident = (int64_t)std::max(1, occ) * di.sm_count * kThrWarps;
+    g->band = pick_band(g->ncb, g->h, resident);
+    const int64_t n = (int64_t)g->ncb * ((g->h + g->band - 1) / g->band);
+    if (n > INT32_MAX) return ME_ERR_ARG;
+    *ntasks = (int)n;
+    *grid = (unsigned)std::max<int64_t>(1, (std::min(n, resident) + kThrWarps - 1) / kThrWarps);
+    return ME_OK;
+}
+
+}  // namespace
+}  // namespace me
+
+extern "C" int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int32_t pitch_bytes,
+                                  int32_t threshold, uint32_t *edge, int32_t stride_words,
+                                  uint32_t *binary, int32_t boundary, me_stream_t stream) {
     TGeo g;
-    g.grey = grey;
-    g.edge = edge;
-    g.binary = binary;
-    g.w = w;
-    g.h = h;
-    g.pitch = pitch_bytes;
-    g.stride = stride_words;
-    g.nw = (int32_t)(((int64_t)w + 31) / 32);
-    g.ncb = (stride_words + kWideLanes - 1) / kWideLanes;
-    g.lastmask = (w & 31) ? ((1u << (w & 31)) - 1u) : kAllOnes;
-    g.fill = boundary == ME_BOUNDARY_WHITE ? kAllOnes : 0u;
+    bool v16 = false;
+    int rc = thr_setup(grey, w, h, pitch_bytes, edge, stride_words, binary, boundary, &g, &v16);
+    if (rc != ME_OK) return rc;
     const uint32_t t = (uint32_t)std::min(std::max(threshold, 1), 255);
     g.t4 = (256u - t) * 0x01010101u;
     const int mode = threshold <= 0 ? 2 : threshold > 255 ? 3 : (t <= 128 ? 1 : 0);
-
-    const bool v16 = ((uintptr_t)grey & 15) == 0 && (pitch_bytes & 15) == 0;
     using Fn = void (*)(TGeo, int);
     static constexpr Fn kFns[2][4] = {
         {k_threshold<false, 0>, k_threshold<false, 1>, k_threshold<false, 2>, k_threshold<false, 3>},
         {k_threshold<true, 0>, k_threshold<true, 1>, k_threshold<true, 2>, k_threshold<true, 3>}};
     const Fn fn = kFns[v16 ? 1 : 0][mode];
-    int occ = 0;
-    if ((rc = cached_occupancy(reinterpret_cast<const void *>(fn), 32 * kThrWarps, 0, &occ)) != ME_OK)
-        return rc;
-    const int64_t resident = (int64_t)std::max(1, occ) * di.sm_count * kThrWarps;
-    g.band = pick_band(g.ncb, h, resident);
-    const int64_t ntasks = (int64_t)g.ncb * ((h + g.band - 1) / g.band);
-    if (ntasks > INT32_MAX) return ME_ERR_ARG;
-    const int64_t grid = std::max<int64_t>(
-        1, (std::min(ntasks, resident) + kThrWarps - 1) / kThrWarps);
-    fn<<<(unsigned)grid, 32 * kThrWarps, 0, (cudaStream_t)stream>>>(g, (int)ntasks);
+    int ntasks = 0;
+    unsigned grid = 0;
+    if ((rc = thr_grid(reinterpret_cast<const void *>(fn), &g, &ntasks, &grid)) != ME_OK) return rc;
+    fn<<<grid, 32 * kThrWarps, 0, (cudaStream_t)stream>>>(g, ntasks);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ME_OK : record_cuda(e);
+}
+
+extern "C" int me_threshold_edges_otsu(const uint8_t *grey, int32_t w, int32_t h,
+                                       int32_t pitch_bytes, uint32_t *edge,
+                                       int32_t stride_words, uint32_t *binary, int32_t boundary,
+                                       int32_t *threshold_out, me_stream_t stream) {
+    TGeo g;
+    bool v16 = false;
+    int rc = thr_setup(grey, w, h, pitch_bytes, edge, stride_words, binary, boundary, &g, &v16);
+    if (rc != ME_OK) return rc;
+    if (threshold_out != nullptr) {
+        if ((uintptr_t)threshold_out & 3) return ME_ERR_ARG;
+        const size_t in_bytes = (size_t)h * (size_t)pitch_bytes;
+        const size_t out_bytes = (size_t)h * (size_t)stride_words * 4;
+        if (ranges_overlap(threshold_out, 4, grey, in_bytes) ||
+            ranges_overlap(threshold_out, 4, edge, out_bytes) ||
+            (binary != nullptr && ranges_overlap(threshold_out, 4, binary, out_bytes)))
+            return ME_ERR_ALIAS;
+        if ((rc = check_device_ptr(threshold_out)) != ME_OK) return rc;
+    }
+    const auto fn = v16 ? k_threshold_dev<true> : k_threshold_dev<false>;
+    int ntasks = 0;
+    unsigned grid = 0;
+    if ((rc = thr_grid(reinterpret_cast<const void *>(fn), &g, &ntasks, &grid)) != ME_OK) return rc;
+    DevInfo di;
+    if ((rc = device_info(&di)) != ME_OK) return rc;
+    const cudaStream_t s = (cudaStream_t)stream;
+    // scratch: the histogram (256 counters) and, if the caller gave no
+    // place for it, the threshold
+    unsigned long long *hist = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&hist), 256 * 8 + 16, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return record_cuda(e);
+    }
+    int32_t *t_dev = threshold_out != nullptr ? threshold_out : reinterpret_cast<int32_t *>(hist + 256);
+    e = cudaMemsetAsync(hist, 0, 256 * 8, s);
+    if (e == cudaSuccess) {
+        const unsigned hgrid = (unsigned)std::max<int64_t>(
+            1, std::min<int64_t>(((int64_t)h + kHistWarps - 1) / kHistWarps, (int64_t)di.sm_count * 4));
+        if (v16)
+            k_grey_hist<true><<<hgrid, 32 * kHistWarps, 0, s>>>(grey, w, h, pitch_bytes, hist);
+        else
+            k_grey_hist<false><<<hgrid, 32 * kHistWarps, 0, s>>>(grey, w, h, pitch_bytes, hist);
+        k_otsu<<<1, 256, 0, s>>>(hist, t_dev);
+        fn<<<grid, 32 * kThrWarps, 0, s>>>(g, ntasks, t_dev);
+        e = cudaGetLastError();
+    }
+    const cudaError_t f = cudaFreeAsync(hist, s);
+    if (e == cudaSuccess) e = f;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return record_cuda(e);
+    }
+    return ME_OK;
 }
