@@ -774,10 +774,19 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
     t_e2e = (time.perf_counter() - t0) / e2e_reps
     e2e_exact = bool(np.array_equal(host_out.numpy(), dev_out.cpu().numpy()))
+    # the host link itself on this machine: plain pinned copies of the same bytes
+    # (the end-to-end number cannot beat these; the link differs by box)
+    link = {}
+    scratch = torch.empty_like(dev_in)
+    for name, fn in (("h2d_gb_s", lambda: scratch.copy_(host_in, non_blocking=True)),
+                     ("d2h_gb_s", lambda: host_out.copy_(dev_out, non_blocking=True))):
+        fn()
+        link[name] = round(host_in.numel() * 4 / time_events(fn, 5, stream) / 1e9, 1)
+    del scratch
     e2e = {"value": round(total_pixels / reduce_max(dist, t_e2e, device) / 1e9, 3),
            "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
            "d2h_bytes_per_step": int(host_out.numel() * 4),
-           "ms_per_step": round(t_e2e * 1e3, 3), "exact": e2e_exact,
+           "ms_per_step": round(t_e2e * 1e3, 3), "exact": e2e_exact, "host_link": link,
            "path": "pinned host buffers -> me_edges_batch_host (chunked, copies overlapped "
                    "with the kernel) -> pinned host buffers"}
 
