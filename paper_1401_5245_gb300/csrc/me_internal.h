@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libme.
 #pragma once
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 
@@ -110,6 +111,36 @@ inline size_t arena_bytes(int n) {
 }
 // Tiles per chunk of a register-window batch configuration.
 inline int chunk_of(const me_tile_cfg &c) { return c.chunk_tiles > 0 ? c.chunk_tiles : 4; }
+
+constexpr int kThrRows = 4;     // rows per step of the threshold kernel's walk
+
+// The threshold kernel's rows per band: the multiple of kThrRows that
+// minimises the walk's length, counted in rows per warp: the waves of tasks
+// (ncb column blocks times the bands of h rows) over the resident warps
+// times the rows one task reads (band + 2) plus about four rows' worth of
+// set-up.  For k waves the shortest band that fits is found directly; k
+// runs from the fewest waves possible (one band per column block:
+// ceil(ncb / resident_warps)) over at most 1024 wave counts, which reaches
+// the optimum over every band height in all cases tried (tests/host).
+inline int threshold_band(int64_t ncb, int32_t h, int64_t resident_warps) {
+    const int64_t max_waves = (ncb * (((int64_t)h + kThrRows - 1) / kThrRows) +
+                               resident_warps - 1) / resident_warps;
+    const int64_t min_waves = std::max<int64_t>(1, (ncb + resident_warps - 1) / resident_warps);
+    int best = kThrRows;
+    int64_t best_cost = INT64_MAX;
+    for (int64_t k = min_waves; k <= std::min<int64_t>(max_waves, min_waves + 1023); ++k) {
+        const int64_t bands = std::max<int64_t>(1, k * resident_warps / ncb);   // per column
+        int64_t band = ((int64_t)h + bands - 1) / bands;
+        band = std::max<int64_t>(kThrRows, (band + kThrRows - 1) / kThrRows * kThrRows);
+        const int64_t tasks = ncb * (((int64_t)h + band - 1) / band);
+        const int64_t cost = (tasks + resident_warps - 1) / resident_warps * (band + 2 + 4);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = (int)std::min<int64_t>(band, INT32_MAX);
+        }
+    }
+    return best;
+}
 
 // ---------------------------------------------------------------- helpers
 // (inline: a batch plan runs them once per image on every call)

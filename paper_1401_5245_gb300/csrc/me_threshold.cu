@@ -21,7 +21,6 @@ namespace me {
 
 namespace {
 
-constexpr int kThrRows = 4;     // rows per step of the walk
 constexpr int kThrWarps = 8;    // warps per CTA
 
 struct TGeo {
@@ -333,28 +332,6 @@ k_otsu(const unsigned long long *__restrict__ hist, int32_t *__restrict__ t_out)
     if (i == 0) *t_out = best_d[0] < 0.0 ? single : best_t[0];
 }
 
-// Rows per band: the multiple of kThrRows that minimises the walk's length,
-// counted in rows per warp: the waves of tasks over the resident warps times
-// the rows one task reads (band + 2) plus about four rows' worth of set-up.
-// For k waves the shortest band that fits is found directly, for k up to 64.
-int pick_band(int64_t ncb, int32_t h, int64_t resident_warps) {
-    const int64_t min_band_waves = (ncb * (((int64_t)h + kThrRows - 1) / kThrRows) +
-                                    resident_warps - 1) / resident_warps;
-    int best = kThrRows;
-    int64_t best_cost = INT64_MAX;
-    for (int64_t k = 1; k <= std::min<int64_t>(min_band_waves, 64); ++k) {
-        const int64_t bands = std::max<int64_t>(1, k * resident_warps / ncb);   // per column
-        int64_t band = ((int64_t)h + bands - 1) / bands;
-        band = std::max<int64_t>(kThrRows, (band + kThrRows - 1) / kThrRows * kThrRows);
-        const int64_t tasks = ncb * (((int64_t)h + band - 1) / band);
-        const int64_t cost = (tasks + resident_warps - 1) / resident_warps * (band + 2 + 4);
-        if (cost < best_cost) {
-            best_cost = cost;
-            best = (int)std::min<int64_t>(band, INT32_MAX);
-        }
-    }
-    return best;
-}
 
 }  // namespace
 
@@ -409,7 +386,7 @@ int thr_grid(const void *fn, TGeo *g, int *ntasks, unsigned *grid) {
     int occ = 0;
     if ((rc = cached_occupancy(fn, 32 * kThrWarps, 0, &occ)) != ME_OK) return rc;
     const int64_t resident = (int64_t)std::max(1, occ) * di.sm_count * kThrWarps;
-    g->band = pick_band(g->ncb, g->h, resident);
+    g->band = threshold_band(g->ncb, g->h, resident);
     const int64_t n = (int64_t)g->ncb * ((g->h + g->band - 1) / g->band);
     if (n > INT32_MAX) return ME_ERR_ARG;
     *ntasks = (int)n;
