@@ -93,9 +93,10 @@ int me_version(void);
  * Each input word is read once from HBM and each output word written once.
  *
  * img, edge     device pointers to h rows of stride_words words each; they
- *               must not overlap (ME_ERR_ALIAS).  128-bit loads are used
- *               when both are 16-byte aligned and stride_words % 4 == 0,
- *               32-bit loads otherwise; both give the same bits.
+ *               must not overlap (ME_ERR_ALIAS).  128-bit accesses are
+ *               used when both are 16-byte aligned and stride_words % 4 == 0,
+ *               64-bit ones when both are 8-byte aligned and stride_words is
+ *               even, 32-bit ones otherwise; all give the same bits.
  * w, h          image size in pixels, each >= 1.
  * stride_words  words per row, >= ceil(w / 32).
  * boundary      ME_BOUNDARY_WHITE or ME_BOUNDARY_BLACK.
@@ -265,7 +266,8 @@ typedef struct me_desc {
  * overlap within each descriptor but not against one another: two
  * descriptors writing the same edge words race.  Images are split into
  * warp tiles (rows x word columns) that the launch walks in one pass;
- * 128-bit loads are used per image where its buffers allow them.
+ * 128-bit (else 64-bit) accesses are used per image where its buffers
+ * allow them, as for me_edges.
  *
  * The library owns a pinned staging ring, a device descriptor arena and a
  * graph cache keyed by (capacity bucket, tile configuration); all of them
@@ -336,8 +338,10 @@ typedef struct me_tile_cfg {
     int32_t rows_per_lane;   /* REGS: rows one lane walks: 4, 8, 16 or 32 */
     int32_t vec_words;       /* REGS: 4 = four words per lane, moved as one
                                 128-bit access where both buffers are 16-byte
-                                aligned and stride_words % 4 == 0, else as
-                                four 32-bit accesses; 1 = 32-bit accesses only
+                                aligned and stride_words % 4 == 0, as two
+                                64-bit accesses where they are 8-byte aligned
+                                and stride_words is even, else as four 32-bit
+                                accesses; 1 = 32-bit accesses only
                                 (single images: one word per lane; batches:
                                 four words per lane) */
     int32_t cta_threads;     /* 128, 256 or 512 */

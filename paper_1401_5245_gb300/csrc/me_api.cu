@@ -161,7 +161,7 @@ static int single_call(int mode, const uint32_t *img, int32_t w, int32_t h,
     if ((rc = check_device_ptr(out)) != ME_OK) return rc;
     const me_tile_cfg cfg = tile_cfg(ME_KIND_SINGLE);
     const Geo g = make_geo(img, w, h, stride_words, boundary, pick_vw(cfg.vec_words),
-                           vec16_ok(img, out, stride_words));
+                           vec16_ok(img, out, stride_words), vec8_ok(img, out, stride_words));
     cudaError_t e;
     if (mode == MODE_EDGE && cfg.engine == ME_ENGINE_BULK) {
         e = launch_bulk(g, out, cfg, (cudaStream_t)stream);
@@ -207,8 +207,13 @@ int me_fundamental_edges(const uint32_t *img, int32_t w, int32_t h,
         if ((rc = check_device_ptr(outs[k])) != ME_OK) return rc;
     const me_tile_cfg cfg = tile_cfg(ME_KIND_SINGLE);
     bool vec16 = true;
-    for (int k = 0; k < 4; ++k) vec16 = vec16 && vec16_ok(img, outs[k], stride_words);
-    const Geo g = make_geo(img, w, h, stride_words, boundary, pick_vw(cfg.vec_words), vec16);
+    bool vec8 = true;
+    for (int k = 0; k < 4; ++k) {
+        vec16 = vec16 && vec16_ok(img, outs[k], stride_words);
+        vec8 = vec8 && vec8_ok(img, outs[k], stride_words);
+    }
+    const Geo g = make_geo(img, w, h, stride_words, boundary, pick_vw(cfg.vec_words), vec16,
+                           vec8);
     Outs o = {{left, right, up, down}};
     cudaError_t e = launch_window(MODE_FUND, g, o, cfg, (cudaStream_t)stream);
     return e == cudaSuccess ? ME_OK : record_cuda(e);

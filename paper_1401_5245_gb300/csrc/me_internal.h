@@ -35,6 +35,7 @@ struct Geo {
     uint32_t fill;              // outside colour as a word: ~0 white, 0 black
     int32_t vw;                 // words per lane and row: 4 or 1
     int32_t vec16;              // vw == 4: the 4 words move as one 128-bit access
+    int32_t vec8;               // vw == 4, not vec16: as two 64-bit accesses
     int32_t nv;                 // vector columns written: ceil(stride / vw)
     int32_t seg_w;              // lanes one row segment uses (nv, or 32 when wide)
     int32_t segs;               // row segments stacked in one warp (32 / seg_w)
@@ -167,9 +168,14 @@ inline int check_image_args(const void *img, const void *out, int32_t w, int32_t
 // Words per lane and row: 4 unless the configuration asks for 1.
 inline int pick_vw(int want_vw) { return want_vw == 4 ? 4 : 1; }
 // A lane's 4 words move as one 128-bit access when both buffers are 16-byte
-// aligned and rows hold whole 16-byte groups, else as four 32-bit accesses.
+// aligned and rows hold whole 16-byte groups; as two 64-bit accesses when
+// they are 8-byte aligned and rows hold whole pairs of words; else as four
+// 32-bit accesses.
 inline bool vec16_ok(const void *img, const void *out, int32_t stride) {
     return !(((uintptr_t)img & 15) || ((uintptr_t)out & 15) || (stride & 3));
+}
+inline bool vec8_ok(const void *img, const void *out, int32_t stride) {
+    return !(((uintptr_t)img & 7) || ((uintptr_t)out & 7) || (stride & 1));
 }
 
 struct DevInfo {
@@ -180,9 +186,10 @@ struct DevInfo {
 };
 int device_info(DevInfo *out);          // current device, cached
 
-// vw is 1 or 4; vec16 (vw == 4 only): 128-bit accesses allowed.
+// vw is 1 or 4; vec16 / vec8 (vw == 4 only): 128-bit / 64-bit accesses
+// allowed (the wider one is taken).
 inline Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
-                    int32_t boundary, int vw, bool vec16 = false) {
+                    int32_t boundary, int vw, bool vec16 = false, bool vec8 = false) {
     // segments of a row of n <= 32 vector columns that fit in a warp: 32 / n
     static constexpr int8_t kSegs[33] = {0, 32, 16, 10, 8, 6, 5, 4, 4, 3, 3, 2, 2, 2, 2, 2, 2,
                                          1, 1,  1,  1,  1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
@@ -196,6 +203,7 @@ inline Geo make_geo(const uint32_t *img, int32_t w, int32_t h, int32_t stride,
     g.fill = (boundary == ME_BOUNDARY_WHITE) ? kAllOnes : 0u;
     g.vw = vw;
     g.vec16 = vw == 4 && vec16;
+    g.vec8 = vw == 4 && !vec16 && vec8;
     g.nv = vw == 4 ? (stride + 3) >> 2 : stride;   // output covers the whole stride
     // narrow rows: segments of exactly nv lanes, as many as fit in a warp
     g.seg_w = g.nv > 32 ? 32 : g.nv;

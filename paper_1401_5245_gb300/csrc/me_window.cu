@@ -14,7 +14,7 @@ namespace me {
 // ------------------------------------------------------------ single image
 // Warp tiles are numbered with the column block fastest, so warps that run
 // together cover whole row bands and share the halo rows in L2.
-template <int VW, int RPT, int MODE, bool V16>
+template <int VW, int RPT, int MODE, int VEC>
 __global__ void __launch_bounds__(512)
 k_window(Geo g, Outs o, int ntasks) {
     const int lane = threadIdx.x & 31;
@@ -23,30 +23,30 @@ k_window(Geo g, Outs o, int ntasks) {
     for (int t = warp; t < ntasks; t += nwarps) {
         const int rb = (int)(((uint64_t)t * g.ncb_m) >> g.ncb_s);    // t / ncb
         const int cb = t - rb * g.ncb;
-        window_tile<VW, RPT, MODE, V16>(g, o, cb, rb, lane);
+        window_tile<VW, RPT, MODE, VEC>(g, o, cb, rb, lane);
     }
 }
 
 using WindowFn = void (*)(Geo, Outs, int);
 
-template <int VW, int MODE, bool V16>
+template <int VW, int MODE, int VEC>
 static WindowFn pick_rpt(int rpt) {
     switch (rpt) {
-        case 4: return k_window<VW, 4, MODE, V16>;
-        case 8: return k_window<VW, 8, MODE, V16>;
-        case 16: return k_window<VW, 16, MODE, V16>;
-        case 32: return k_window<VW, 32, MODE, V16>;
+        case 4: return k_window<VW, 4, MODE, VEC>;
+        case 8: return k_window<VW, 8, MODE, VEC>;
+        case 16: return k_window<VW, 16, MODE, VEC>;
+        case 32: return k_window<VW, 32, MODE, VEC>;
         default: return nullptr;
     }
 }
 
-template <int VW, bool V16>
+template <int VW, int VEC>
 static WindowFn pick_mode(int mode, int rpt) {
     switch (mode) {
-        case MODE_EDGE: return pick_rpt<VW, MODE_EDGE, V16>(rpt);
-        case MODE_DISPLAY: return pick_rpt<VW, MODE_DISPLAY, V16>(rpt);
-        case MODE_FUND: return pick_rpt<VW, MODE_FUND, V16>(rpt);
-        case MODE_END: return pick_rpt<VW, MODE_END, V16>(rpt);
+        case MODE_EDGE: return pick_rpt<VW, MODE_EDGE, VEC>(rpt);
+        case MODE_DISPLAY: return pick_rpt<VW, MODE_DISPLAY, VEC>(rpt);
+        case MODE_FUND: return pick_rpt<VW, MODE_FUND, VEC>(rpt);
+        case MODE_END: return pick_rpt<VW, MODE_END, VEC>(rpt);
         default: return nullptr;
     }
 }
@@ -61,9 +61,10 @@ static int64_t tasks_of(int h, int segs, int ncb, int rpt) {
 
 cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
                           const me_tile_cfg &cfg, cudaStream_t s) {
-    WindowFn fn = g.vw != 4 ? pick_mode<1, false>(mode, cfg.rows_per_lane)
-                  : g.vec16 ? pick_mode<4, true>(mode, cfg.rows_per_lane)
-                            : pick_mode<4, false>(mode, cfg.rows_per_lane);
+    WindowFn fn = g.vw != 4 ? pick_mode<1, 4>(mode, cfg.rows_per_lane)
+                  : g.vec16 ? pick_mode<4, 16>(mode, cfg.rows_per_lane)
+                  : g.vec8  ? pick_mode<4, 8>(mode, cfg.rows_per_lane)
+                            : pick_mode<4, 4>(mode, cfg.rows_per_lane);
     if (fn == nullptr) return cudaErrorInvalidValue;
     const int64_t ntasks = tasks_of(g.h, g.segs, g.ncb, cfg.rows_per_lane);
     if (ntasks > INT32_MAX) return cudaErrorInvalidValue;
@@ -141,7 +142,8 @@ k_batch(const BatchHeader *__restrict__ hdr) {
             g.lastmask = d2.x;
             g.fill = d2.y;
             g.vw = (int)(d2.z & 0xff);
-            g.vec16 = (int)(d2.z >> 8);
+            g.vec16 = (int)((d2.z >> 8) & 1);
+            g.vec8 = (int)((d2.z >> 9) & 1);
             g.seg_w = (int)d2.w;
             g.ncb = (int)d3.x;
             g.nv = (int)d3.y;
@@ -153,11 +155,14 @@ k_batch(const BatchHeader *__restrict__ hdr) {
             // division
             const int cb = g.ncb == 1 ? 0 : local % g.ncb;
             const int rb = g.ncb == 1 ? local : local / g.ncb;
-            if (g.vec16)
-                window_tile<4, RPT, MODE_EDGE, true>(g, o, cb, rb, lane);
-            else if constexpr (ANY)
-                window_tile<4, RPT, MODE_EDGE, false>(g, o, cb, rb, lane);
-            else if (lane == 0)
+            if (g.vec16) {
+                window_tile<4, RPT, MODE_EDGE, 16>(g, o, cb, rb, lane);
+            } else if constexpr (ANY) {
+                if (g.vec8)
+                    window_tile<4, RPT, MODE_EDGE, 8>(g, o, cb, rb, lane);
+                else
+                    window_tile<4, RPT, MODE_EDGE, 4>(g, o, cb, rb, lane);
+            } else if (lane == 0)
                 atomicOr(&g_me_window_faults, kFaultUnalignedTile);
         }
     }
@@ -239,7 +244,8 @@ static void fill_bdesc(const me_desc &d, const me_tile_cfg &cfg, BDesc *out) {
     // batches always take 4 words per lane; vec_words = 1 asks for 32-bit
     // accesses
     Geo g = make_geo(d.img, d.w, d.h, d.stride_words, d.boundary, 4,
-                     cfg.vec_words == 4 && vec16_ok(d.img, d.edge, d.stride_words));
+                     cfg.vec_words == 4 && vec16_ok(d.img, d.edge, d.stride_words),
+                     cfg.vec_words == 4 && vec8_ok(d.img, d.edge, d.stride_words));
     out->img = d.img;
     out->edge = d.edge;
     out->segs = g.segs;
@@ -248,7 +254,8 @@ static void fill_bdesc(const me_desc &d, const me_tile_cfg &cfg, BDesc *out) {
     out->nw = g.nw;
     out->lastmask = g.lastmask;
     out->fill = g.fill;
-    out->vw = g.vw | (g.vec16 << 8);     // words per lane, and 128-bit accesses
+    // words per lane; 128-bit (bit 8) or 64-bit (bit 9) accesses
+    out->vw = g.vw | (g.vec16 << 8) | (g.vec8 << 9);
     out->seg_w = g.seg_w;
     out->ncb = g.ncb;
     out->nv = g.nv;

@@ -93,9 +93,10 @@ __device__ __forceinline__ Lane<VW> make_lane(const Geo &g, const Outs &o, int c
     return L;
 }
 
-// Row y into registers.  CHECK: y may lie outside [0, h).  V16 (VW == 4):
-// one 128-bit load, else four 32-bit loads.
-template <int VW, bool CHECK, bool V16>
+// Row y into registers.  CHECK: y may lie outside [0, h).  VEC (VW == 4):
+// the bytes per access -- 16: one 128-bit load; 8: two 64-bit loads; 4: four
+// 32-bit loads.
+template <int VW, bool CHECK, int VEC>
 __device__ __forceinline__ Words<VW> load_row(const Lane<VW> &L, int y) {
     Words<VW> r;
     const bool rowok = !CHECK || (unsigned)y < (unsigned)L.h;
@@ -104,10 +105,26 @@ __device__ __forceinline__ Words<VW> load_row(const Lane<VW> &L, int y) {
     uint32_t raw[VW];
     if constexpr (VW == 4) {
         uint4 q = make_uint4(0, 0, 0, 0);
-        if constexpr (V16) {
+        if constexpr (VEC == 16) {
             // 16-byte aligned: img is, stride % 4 == 0 and c0 % 4 == 0; the
             // four words stay inside the row's stride.
             if (ok) q = __ldg(reinterpret_cast<const uint4 *>(p));
+        } else if constexpr (VEC == 8) {
+            // 8-byte aligned: img is, stride and c0 are even.  A pair that
+            // starts at a word with pixels (below nw <= stride) ends inside
+            // the stride; pairs without pixels are not read.
+            if (ok) {
+                if (L.keep[0]) {
+                    const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p));
+                    q.x = a.x;
+                    q.y = a.y;
+                }
+                if (L.keep[2]) {
+                    const uint2 b = __ldg(reinterpret_cast<const uint2 *>(p) + 1);
+                    q.z = b.x;
+                    q.w = b.y;
+                }
+            }
         } else if (ok) {
             // one word at a time; words without pixels are not read
             if (L.keep[0]) q.x = __ldg(p);
@@ -115,7 +132,7 @@ __device__ __forceinline__ Words<VW> load_row(const Lane<VW> &L, int y) {
             if (L.keep[2]) q.z = __ldg(p + 2);
             if (L.keep[3]) q.w = __ldg(p + 3);
         }
-        raw[0] = q.x; raw[1] = q.y; raw[2] = q.z; raw[3] = q.w;
+    raw[0] = q.x; raw[1] = q.y; raw[2] = q.z; raw[3] = q.w;
     } else {
         raw[0] = ok ? __ldg(p) : 0u;
     }
@@ -139,16 +156,21 @@ __device__ __forceinline__ void side_words(const Lane<VW> &L, const Words<VW> &r
     next = L.seg_last ? L.fill : b;
 }
 
-template <int VW, bool V16>
+template <int VW, int VEC>
 __device__ __forceinline__ void store_words(const Lane<VW> &L, uint32_t *out, int y,
                                             const uint32_t (&e)[VW]) {
     // Padding words (nw .. stride-1) are written too, as 0, so every 32-byte
     // sector of an output row is written whole and never read back.
     uint32_t *p = out + (size_t)y * (size_t)L.stride;
     if constexpr (VW == 4) {
-        if constexpr (V16) {
+        if constexpr (VEC == 16) {
             // stride % 4 == 0: the group lies inside the row
             __stcs(reinterpret_cast<uint4 *>(p), make_uint4(e[0], e[1], e[2], e[3]));
+        } else if constexpr (VEC == 8) {
+            // stride and c0 even: the group's words inside the stride are
+            // whole pairs, at least one
+            __stcs(reinterpret_cast<uint2 *>(p), make_uint2(e[0], e[1]));
+            if (L.nst > 2) __stcs(reinterpret_cast<uint2 *>(p) + 1, make_uint2(e[2], e[3]));
         } else {
             // the words of the group inside the stride, one at a time
             __stcs(p, e[0]);
@@ -163,7 +185,7 @@ __device__ __forceinline__ void store_words(const Lane<VW> &L, uint32_t *out, in
 
 // One output row from the rows above (u), at (c) and below (d); cp/cn are
 // the words beside c, up_*/dn_* beside u and d (end points only).
-template <int VW, int MODE, bool V16>
+template <int VW, int MODE, int VEC>
 __device__ __forceinline__ void emit_row(const Lane<VW> &L, int y, const Words<VW> &u,
                                          const Words<VW> &c, const Words<VW> &d, uint32_t cp,
                                          uint32_t cn, uint32_t up_p, uint32_t up_n,
@@ -217,17 +239,17 @@ __device__ __forceinline__ void emit_row(const Lane<VW> &L, int y, const Words<V
             e0[k] = M & ~two & valid;
         }
     }
-    store_words<VW, V16>(L, L.out[0], y, e0);
+    store_words<VW, VEC>(L, L.out[0], y, e0);
     if constexpr (MODE == MODE_FUND) {
-        store_words<VW, V16>(L, L.out[1], y, e1);
-        store_words<VW, V16>(L, L.out[2], y, e2);
-        store_words<VW, V16>(L, L.out[3], y, e3);
+        store_words<VW, VEC>(L, L.out[1], y, e1);
+        store_words<VW, VEC>(L, L.out[2], y, e2);
+        store_words<VW, VEC>(L, L.out[3], y, e3);
     }
 }
 
 // One warp tile: column block cb, row block rb of image g.  CHECK: the
 // tile's rows, with one halo row above and below, may leave the image.
-template <int VW, int RPT, int MODE, bool CHECK, bool V16>
+template <int VW, int RPT, int MODE, bool CHECK, int VEC>
 __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, int cb, int rb,
                                                  int lane) {
     constexpr int PF = prefetch_rows(RPT);
@@ -243,11 +265,11 @@ __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, in
     const Lane<VW> L = make_lane<VW>(g, o, seg < g.segs ? v * VW : -VW, col, g.seg_w, owner);
     const bool rows_left = !CHECK || y0 < g.h;    // the segment has rows
 
-    Words<VW> up = load_row<VW, CHECK, V16>(L, y0 - 1);
-    Words<VW> cur = load_row<VW, CHECK, V16>(L, y0);
+    Words<VW> up = load_row<VW, CHECK, VEC>(L, y0 - 1);
+    Words<VW> cur = load_row<VW, CHECK, VEC>(L, y0);
     Words<VW> q[PF];
 #pragma unroll
-    for (int i = 0; i < PF; ++i) q[i] = load_row<VW, CHECK, V16>(L, y0 + 1 + i);
+    for (int i = 0; i < PF; ++i) q[i] = load_row<VW, CHECK, VEC>(L, y0 + 1 + i);
     uint32_t up_p = 0, up_n = 0, cur_p, cur_n;
     if constexpr (MODE == MODE_END) side_words<VW>(L, up, up_p, up_n);
     side_words<VW>(L, cur, cur_p, cur_n);
@@ -258,11 +280,11 @@ __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, in
         for (int j = 0; j < PF; ++j) {
             const int y = y0 + r0 + j;
             const Words<VW> dn = q[j];
-            if (r0 + j + 1 + PF <= RPT) q[j] = load_row<VW, CHECK, V16>(L, y + 1 + PF);
+            if (r0 + j + 1 + PF <= RPT) q[j] = load_row<VW, CHECK, VEC>(L, y + 1 + PF);
             uint32_t dn_p, dn_n;
             side_words<VW>(L, dn, dn_p, dn_n);
             if (L.writes && rows_left && (!CHECK || y < g.h))
-                emit_row<VW, MODE, V16>(L, y, up, cur, dn, cur_p, cur_n, up_p, up_n, dn_p, dn_n);
+                emit_row<VW, MODE, VEC>(L, y, up, cur, dn, cur_p, cur_n, up_p, up_n, dn_p, dn_n);
             up = cur;
             cur = dn;
             up_p = cur_p;
@@ -273,15 +295,15 @@ __device__ __forceinline__ void window_tile_rows(const Geo &g, const Outs &o, in
     }
 }
 
-template <int VW, int RPT, int MODE, bool V16>
+template <int VW, int RPT, int MODE, int VEC>
 __device__ __forceinline__ void window_tile(const Geo &g, const Outs &o, int cb, int rb,
                                             int lane) {
     const int rows_per_task = RPT * g.segs;
     const int top = rb * rows_per_task;
     if (top >= 1 && top + rows_per_task < g.h)
-        window_tile_rows<VW, RPT, MODE, false, V16>(g, o, cb, rb, lane);
+        window_tile_rows<VW, RPT, MODE, false, VEC>(g, o, cb, rb, lane);
     else
-        window_tile_rows<VW, RPT, MODE, true, V16>(g, o, cb, rb, lane);
+        window_tile_rows<VW, RPT, MODE, true, VEC>(g, o, cb, rb, lane);
 }
 
 }  // namespace me
