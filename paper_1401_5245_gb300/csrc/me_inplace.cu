@@ -217,15 +217,23 @@ constexpr size_t inplace_smem(int threads) {
 
 template <int C, bool V16, int Q, int G>
 cudaError_t launch_inplace(const IpGeo &g, int threads, cudaStream_t s) {
-    // the ring exceeds the default 48 KiB for wide rows; raise the limit once
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(k_inplace<C, V16, Q, G>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)inplace_smem<C, Q>(kIpMaxThreads));
-    });
-    if (attr != cudaSuccess) return attr;
+    // the ring exceeds the default 48 KiB for wide rows; raise the limit
+    // once per device (the attribute belongs to the device's context)
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 64 || !done[dev]) {
+            e = cudaFuncSetAttribute(k_inplace<C, V16, Q, G>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)inplace_smem<C, Q>(kIpMaxThreads));
+            if (e != cudaSuccess) return e;
+            if (dev < 64) done[dev] = true;
+        }
+    }
     k_inplace<C, V16, Q, G><<<g.nbands, threads, inplace_smem<C, Q>(threads), s>>>(g);
     return cudaGetLastError();
 }
