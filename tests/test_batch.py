@@ -96,7 +96,9 @@ def test_small_uneven_batch(pad16):
     check_batch(imgs, srcs, dsts)
 
 
-def test_misaligned_buffers_take_the_32bit_path():
+def test_misaligned_buffers_take_the_narrower_paths():
+    """Buffers 0, 1, 2 and 3 words past the 16-byte grid: 128-bit, 32-bit,
+    64-bit and 32-bit accesses in one launch."""
     imgs, srcs, dsts, items = make_batch(2, 40, 1, 300, True, offs=[0, 1, 2, 3])
     assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
     sync()
@@ -137,7 +139,7 @@ def batch_cfgs():
 def test_every_batch_configuration():
     L = _lib.load()
     saved = _lib.me_get_tile_cfg(1)
-    imgs, srcs, dsts, items = make_batch(3, 50, 1, 1200, offs=[0, 0, 0, 1])
+    imgs, srcs, dsts, items = make_batch(3, 50, 1, 1200, offs=[0, 0, 2, 1])
     # one very wide image forces column strips in the bulk engine
     wide = (np.random.default_rng(9).random((21, 30000)) < 0.5).astype(np.uint8)
     words = S.pack(wide, S.batch_stride(30000), pad="random", seed=3)

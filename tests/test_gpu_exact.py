@@ -171,8 +171,9 @@ def all_single_cfgs():
 
 def test_every_tile_configuration():
     """Every engine and tile shape on ragged images: whole-row bands,
-    column strips (rows wider than a stage), unaligned rows (cooperative
-    loads, 32-bit stores) and tiny images."""
+    column strips (rows wider than a stage), rows of 16-byte groups, of word
+    pairs (64-bit accesses) and unaligned rows (cooperative loads, 32-bit
+    stores), and tiny images."""
     L = _lib.load()
     saved = _lib.me_get_tile_cfg(0)
     shapes = [(97, 45), (4100, 37), (300, 129), (33, 1000), (1, 70), (40000, 19)]
@@ -182,6 +183,10 @@ def test_every_tile_configuration():
         ref = O.edges(img, 0)
         cases.append((img, ref, S.round_up(S.words_per_row(w), 4), 0))
         cases.append((img, ref, S.words_per_row(w) + 1, 1))
+        # 64-bit pairs: an even stride off the 16-byte grid, and 16-byte
+        # rows in buffers 8 bytes past it
+        cases.append((img, ref, S.round_up(S.words_per_row(w), 4) + 2, 0))
+        cases.append((img, ref, S.round_up(S.words_per_row(w), 4), 2))
     try:
         for c in all_single_cfgs():
             assert _lib.me_set_tile_cfg(0, _lib.me_tile_cfg(*c)) == 0, c
@@ -223,7 +228,8 @@ def fund_call(img, w, h, stride, l, r, u, d, boundary, stream):
 def test_fundamental_edges(w, h):
     img = rand_img(w * h, h, w, 0.5)
     for boundary in (0, 1):
-        for stride in (S.words_per_row(w), S.round_up(S.words_per_row(w), 4)):
+        for stride in (S.words_per_row(w), S.round_up(S.words_per_row(w), 4),
+                       S.round_up(S.words_per_row(w), 4) + 2):
             got = run_single(fund_call, img, stride=stride, boundary=boundary, n_out=4)
             want = O.fundamental(img, boundary)
             for name, g_, w_ in zip(("left", "right", "up", "down"), got, want):
