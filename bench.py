@@ -885,7 +885,8 @@ def run_profile_case(case: str, launches: int, cfg: str | None = None):
     capture (inputs still larger than L2): 'batch' = the 4096-image batch
     kernel; 'single' = me_edges on one 32768 x 32768 image (256 MiB);
     'inplace' = me_edges_inplace on that image; 'threshold' =
-    me_threshold_edges on a 16384 x 16384 grey image (256 MiB).
+    me_threshold_edges on a 16384 x 16384 grey image (256 MiB); 'otsu' =
+    me_threshold_edges_otsu on that image.
     cfg: optional tile configuration 'engine,rows,vec,threads,ctas,kb,stages[,chunk]'."""
     import torch
     import __graft_entry__
@@ -924,6 +925,16 @@ def run_profile_case(case: str, launches: int, cfg: str | None = None):
             _lib.check(lib.me_edges_inplace(x.data_ptr(), w, h, 1024, 0, stream.cuda_stream))
         torch.cuda.synchronize()
         ok = True
+    elif case == "otsu":
+        w = h = 16384
+        g = np.random.default_rng(0)
+        grey = torch.from_numpy(g.integers(0, 256, (h, w), dtype=np.uint8)).to(device)
+        edge = torch.empty((h, w // 32), dtype=torch.int32, device=device)
+        for _ in range(launches):
+            _lib.check(_lib.me_threshold_edges_otsu(grey, w, h, w, edge, w // 32, None, 0, None,
+                                                    stream))
+        torch.cuda.synchronize()
+        ok = True
     else:
         w = h = 16384
         g = np.random.default_rng(0)
@@ -940,7 +951,8 @@ def run_profile_case(case: str, launches: int, cfg: str | None = None):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["batch", "single", "inplace", "threshold"], default=None,
+    ap.add_argument("--profile", choices=["batch", "single", "inplace", "threshold", "otsu"],
+                    default=None,
                     help="run a few launches of one kernel for an ncu capture")
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--cfg", default=None, help="tile configuration for --profile")
