@@ -26,7 +26,7 @@ def lib():
     return _lib
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_entry_points():
     names = declared_functions()
     for n in ("me_edges", "me_edges_batch", "me_serve_open", "me_serve_submit",
               "me_serve_poll", "me_serve_close", "me_status_string"):
