@@ -268,7 +268,7 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_a
     int32_t *block_image = reinterpret_cast<int32_t *>(bd + n);
     std::memset(hdr, 0, sizeof(*hdr));
     int64_t total = 0, bytes = 0;
-    bool words32 = false;       // some image takes 32-bit accesses
+    bool narrow = false;        // some image takes 64- or 32-bit accesses
     for (int i = 0; i < n; ++i) {
         const me_desc &d = descs[i];
         int rc = check_image_args(d.img, d.edge, d.w, d.h, d.stride_words, d.boundary);
@@ -277,7 +277,7 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_a
             return rc;
         }
         fill_bdesc(d, cfg, &bd[i]);
-        words32 |= (bd[i].vw >> 8) == 0;
+        narrow |= ((bd[i].vw >> 8) & 1) == 0;   // not the 128-bit path
         const int64_t nt = tasks_of(bd[i].h, bd[i].segs, bd[i].ncb, cfg.rows_per_lane);
         if (total + nt > INT32_MAX) {
             if (bad) *bad = i;
@@ -307,7 +307,7 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_a
     }
     block_image[b] = n - 1;
     if (total_tasks) *total_tasks = total;
-    if (any) *any = words32;
+    if (any) *any = narrow;
     return ME_OK;
 }
 

@@ -105,6 +105,20 @@ def test_misaligned_buffers_take_the_narrower_paths():
     check_batch(imgs, srcs, dsts)
 
 
+@pytest.mark.parametrize("offs", [[0, 2], [2]])
+def test_batch_of_128_and_64_bit_images_only(offs):
+    """Images on the 128-bit and the 64-bit paths with none on the 32-bit
+    one (buffers 0 or 2 words past the 16-byte grid, rows of 16-byte
+    groups): the plan must still take the kernel form that carries the
+    64-bit tile, and no image may be skipped."""
+    _lib.me_device_faults(clear=True)
+    imgs, srcs, dsts, items = make_batch(4, 60, 1, 500, True, offs=offs)
+    assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
+    sync()
+    check_batch(imgs, srcs, dsts)
+    assert _lib.me_device_faults(clear=True) == 0
+
+
 def test_repeated_calls_reuse_graphs_and_slots():
     """Many calls in a row with different batch sizes: the staging ring
     and the cached graphs are reused while earlier launches may be in
