@@ -769,9 +769,12 @@ def run_ours(args, rank, world, local_rank):
     e2e_step()
     e2e_reps = max(3, min(args.steps, 20))
     barrier(dist)
+    rep_s = []
     t0 = time.perf_counter()
     for _ in range(e2e_reps):
+        t1 = time.perf_counter()
         e2e_step()
+        rep_s.append(time.perf_counter() - t1)
     t_e2e = (time.perf_counter() - t0) / e2e_reps
     e2e_exact = bool(np.array_equal(host_out.numpy(), dev_out.cpu().numpy()))
     # the host link itself on this machine: plain pinned copies of the same bytes
@@ -787,6 +790,9 @@ def run_ours(args, rank, world, local_rank):
            "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
            "d2h_bytes_per_step": int(host_out.numel() * 4),
            "ms_per_step": round(t_e2e * 1e3, 3), "exact": e2e_exact, "host_link": link,
+           "ms_per_rep": {"min": round(min(rep_s) * 1e3, 3),
+                          "median": round(float(np.median(rep_s)) * 1e3, 3),
+                          "max": round(max(rep_s) * 1e3, 3)},
            "path": "pinned host buffers -> me_edges_batch_host (chunked, copies overlapped "
                    "with the kernel) -> pinned host buffers"}
 
