@@ -13,6 +13,10 @@
 // it is consumed, so four rows per warp stay in flight.  The band height is
 // chosen on the host from the number of resident warps (few waves, little
 // idle tail).
+//
+// With Otsu's rule the threshold comes from the image itself, on the
+// device: a histogram pass, one CTA that scores every threshold, and the
+// same walk reading the chosen threshold from device memory.
 #include <algorithm>
 
 #include "me_internal.h"
@@ -226,8 +230,9 @@ constexpr int kHistGroups = 4;  // 16-byte groups per lane in flight
 // atomics bound it: about nine updates of distinct counters per clock per
 // SM, i.e. about 2.7 TB/s of grey on varied images (updates of one counter
 // within a warp merge, so a flat image reads at the copy rate).  A counter
-// column per lane (no bank conflicts at all) and plain read-modify-write
-// in such columns both measured slower.
+// column per lane (no bank conflicts at all) measured no faster on varied
+// images and slower on flat ones; plain read-modify-write in such columns
+// was slower still.
 template <bool V16>
 __global__ void __launch_bounds__(32 * kHistWarps)
 k_grey_hist(const uint8_t *__restrict__ grey, int32_t w, int32_t h, int32_t pitch,
