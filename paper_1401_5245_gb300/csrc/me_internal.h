@@ -57,7 +57,8 @@ struct BDesc {
     uint32_t *edge;
     int32_t segs, h, stride, nw;
     uint32_t lastmask, fill;
-    int32_t vw, seg_w, ncb, nv;
+    int32_t vw;                 // bits 0-7 words per lane; bit 8 128-bit, bit 9 64-bit accesses
+    int32_t seg_w, ncb, nv;
     int32_t task_base, ntasks;
 };
 static_assert(sizeof(BDesc) == 64, "BDesc is 64 bytes");
