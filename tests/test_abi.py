@@ -91,6 +91,17 @@ def test_argument_errors_without_a_gpu(lib):
     for chunk in (-1, 65):                                      # tiles per chunk
         cfg = lib.me_tile_cfg(0, 4, 4, 256, 8, 32, 4, chunk)
         assert L.me_set_tile_cfg(1, ctypes.byref(cfg)) == ARG
+    g = 0x300000                                                # a made-up grey image
+    assert L.me_threshold_edges(None, 64, 4, 64, 128, b, 2, None, 0, None) == ARG
+    assert L.me_threshold_edges(g, 64, 4, 63, 128, b, 2, None, 0, None) == ARG   # pitch < w
+    assert L.me_threshold_edges(g, 64, 4, 64, 128, b, 1, None, 0, None) == ARG   # stride
+    assert L.me_threshold_edges(g, 64, 4, 64, 128, b, 2, None, 2, None) == ARG   # boundary
+    assert L.me_threshold_edges(g, 64, 4, 64, 128, b + 2, 2, None, 0, None) == ARG
+    assert L.me_threshold_edges(g, 64, 4, 64, 128, g + 64, 2, None, 0, None) == ALIAS
+    assert L.me_threshold_edges(g, 64, 4, 64, 128, b, 2, b + 4, 0, None) == ALIAS
+    assert L.me_threshold_edges_otsu(None, 64, 4, 64, b, 2, None, 0, None, None) == ARG
+    assert L.me_threshold_edges_otsu(g, 0, 4, 64, b, 2, None, 0, None, None) == ARG
+    assert L.me_threshold_edges_otsu(g, 64, 4, 64, g + 8, 2, None, 0, None, None) == ALIAS
     assert L.me_serve_open(None, None) == ARG
     assert L.me_serve_poll(None, 1, None, 0, None) == ARG
     assert L.me_serve_close(None, 0) == ARG
