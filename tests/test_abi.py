@@ -43,6 +43,31 @@ def test_every_declared_symbol_is_exported(lib):
     assert sorted(lib.PROTOTYPES) == declared_functions()
 
 
+def test_header_is_c_and_every_entry_point_links_from_c(lib, tmp_path):
+    """A C11 program (strict, warnings as errors) that includes the header
+    and takes the address of every declared function links against the
+    library."""
+    names = declared_functions()
+    src = tmp_path / "uses_every_entry_point.c"
+    src.write_text("#include \"me.h\"\n#include <stdio.h>\n"
+                   "int main(void) {\n"
+                   "    void (*fns[])(void) = {\n" +
+                   "".join(f"        (void (*)(void)){n},\n" for n in names) +
+                   "    };\n"
+                   "    printf(\"%d\\n\", (int)(sizeof fns / sizeof fns[0]));\n"
+                   "    return 0;\n}\n")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    pkg = os.path.dirname(lib.LIB_PATH)
+    exe = tmp_path / "uses_every_entry_point"
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-Wno-cast-function-type",
+                           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"),
+                           str(src), "-L", pkg, "-lme", "-Wl,-rpath," + pkg, "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    assert int(out.stdout) == len(names)
+
+
 def test_library_links_shared_cuda_runtime(lib):
     out = subprocess.run(["readelf", "-d", lib.LIB_PATH], capture_output=True,
                          text=True, check=True).stdout
