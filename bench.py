@@ -449,80 +449,82 @@ def unpadded_leg(lib_mod, stream, peak):
             "exact": exact, "exact_images_checked": n}
 
 
-def serve_leg(lib_mod, n_requests=20000, loads=(0.25, 0.5, 0.8, 0.95), seed=0):
+def serve_leg(lib_mod, n_requests=100000, loads=(0.25, 0.5, 0.8, 0.95), seed=0):
     """Serving: requests drawn from the 48x48 / 1024x1024 / 2480x3508 mix
-    (70/25/5 %), an 8 GiB device budget.  First the closed-loop saturated
-    rate (everything submitted at once), then Poisson arrivals at fractions
-    of it; latency is submit -> result ready (copies included)."""
+    (70/25/5 %), an 8 GiB device budget, driven from C threads by the
+    load generator (libme_loadgen.so) so that the server, not the client,
+    bounds the rate.  First every request of the trace in a closed loop,
+    each result compared with the same image computed alone by me_edges;
+    then the closed-loop saturated rate (clients x window requests
+    outstanding); then Poisson arrivals at fractions of it (open loop).
+    Latency: scheduled arrival (open) or submit (closed) to the poll that
+    delivered the result, copies both ways included."""
+    import torch
     from paper_1401_5245_gb300 import synth
     pool = synth.serve_pool(seed)
     _, cls = synth.serve_trace(seed, n_requests, 1.0)
     g = np.random.default_rng(seed + 1)
     reqs = [pool[c][int(g.integers(0, len(pool[c])))] for c in cls]
-    outs = {id(im): np.empty_like(im.words) for c in pool for im in c}
-    srv = lib_mod.Server(hbm_budget_bytes=8 << 30, staging_bytes=1 << 30, max_inflight=4,
-                         max_batch=256, tick_us=20)
+    alone = {}
+    for im in (x for c in pool for x in c):
+        xd = torch.from_numpy(im.words.view(np.int32)).cuda()
+        yd = torch.zeros_like(xd)
+        lib_mod.check(lib_mod.me_edges(xd, im.w, im.h, im.stride_words, yd, im.boundary))
+        torch.cuda.synchronize()
+        alone[id(im)] = yd.cpu().numpy().view(np.uint32).copy()
+    expect = [alone[id(im)] for im in reqs]
+    cores = os.cpu_count() or 8
+    # the server takes two threads (engine, completion); the rest drive it
+    closed_clients = open_clients = max(2, min(14, cores - 2))
+    window = 16
+    cfg = dict(hbm_budget_bytes=8 << 30, staging_bytes=1 << 30, max_inflight=4,
+               max_batch=512, tick_us=0)
+    srv = lib_mod.Server(**cfg)
     px = sum(im.pixels for im in reqs)
-    result = {"requests": n_requests, "budget_bytes": 8 << 30,
-              "mix": "48x48 70%, 1024x1024 25%, 2480x3508 5%",
-              "mean_pixels": round(px / n_requests)}
-    try:
-        def run(arrivals):
-            tickets = [None] * len(reqs)
-            lat = np.zeros(len(reqs))
-            t0 = time.perf_counter()
+    nbytes = sum(2 * im.packed_bytes for im in reqs)     # in + out over the link
+    result = {"requests_per_point": n_requests, "budget_bytes": cfg["hbm_budget_bytes"],
+              "server_cfg": cfg, "mix": "48x48 70%, 1024x1024 25%, 2480x3508 5%",
+              "mean_pixels": round(px / n_requests),
+              "mean_packed_bytes_each_way": round(nbytes / 2 / n_requests),
+              "driver": "libme_loadgen.so (C threads through the public C ABI)",
+              "closed_clients": closed_clients, "closed_window": window,
+              "open_clients": open_clients}
 
-            def submitter():
-                for i, im in enumerate(reqs):
-                    if arrivals is not None:
-                        d = t0 + arrivals[i] - time.perf_counter()
-                        if d > 0:
-                            time.sleep(d)
-                    rc, tk = srv.submit(im.words, im.w, im.h, im.stride_words)
-                    if rc != 0:
-                        raise lib_mod.MeError(rc, "me_serve_submit")
-                    tickets[i] = tk
-            th = threading.Thread(target=submitter)
-            th.start()
-            for i, im in enumerate(reqs):
-                while tickets[i] is None:
-                    time.sleep(20e-6)
-                rc, tm = srv.poll(tickets[i], outs[id(im)], -1)
-                if rc != 0:
-                    raise lib_mod.MeError(rc, "me_serve_poll")
-                lat[i] = tm.total_us
-            th.join()
-            wall = time.perf_counter() - t0
-            return wall, lat
-        run(None)                                  # warm-up
-        wall, lat = run(None)
-        sat_rate = n_requests / wall
-        result["saturated"] = {"req_per_s": round(sat_rate, 1),
-                               "gpixel_s": round(px / wall / 1e9, 3),
-                               "p50_us": round(float(np.percentile(lat, 50)), 1),
-                               "p99_us": round(float(np.percentile(lat, 99)), 1),
-                               "max_us": round(float(lat.max()), 1)}
+    def point(r, before, after):
+        lat, sv = r["latency_us"], r["server_us"]
+        batches = after["batches"] - before["batches"]
+        done = after["completed"] - before["completed"]
+        return {"req_per_s": round(n_requests / r["wall_s"], 1),
+                "gpixel_s": round(px / r["wall_s"] / 1e9, 2),
+                "host_link_gb_s": round(nbytes / r["wall_s"] / 1e9, 2),
+                "p50_us": round(float(np.nanpercentile(lat, 50)), 1),
+                "p99_us": round(float(np.nanpercentile(lat, 99)), 1),
+                "max_us": round(float(np.nanmax(lat)), 1),
+                "server_p50_us": round(float(np.nanpercentile(sv, 50)), 1),
+                "server_p99_us": round(float(np.nanpercentile(sv, 99)), 1),
+                "requests_per_batch": round(done / max(1, batches), 2),
+                "copies_per_batch": round((after["copies"] - before["copies"]) /
+                                          max(1, batches), 2),
+                "errors": r["errors"]}
+    try:
+        # every result against the same image computed alone
+        r = lib_mod.load_run(srv, reqs, expect=expect, clients=closed_clients, window=window)
+        result["exact"] = r["mismatches"] == 0 and r["errors"] == 0
+        result["exact_requests_checked"] = n_requests
+        st0 = srv.stats()
+        r = lib_mod.load_run(srv, reqs, clients=closed_clients, window=window)
+        st1 = srv.stats()
+        result["saturated"] = point(r, st0, st1)
+        sat_rate = n_requests / r["wall_s"]
         for f in loads:
             t_arr, _ = synth.serve_trace(seed + 7, n_requests, f * sat_rate)
-            wall, lat = run(t_arr)
-            result[f"load_{f}"] = {"offered_req_per_s": round(f * sat_rate, 1),
-                                   "gpixel_s": round(px / wall / 1e9, 3),
-                                   "p50_us": round(float(np.percentile(lat, 50)), 1),
-                                   "p99_us": round(float(np.percentile(lat, 99)), 1),
-                                   "max_us": round(float(lat.max()), 1)}
-        # results equal the same images computed alone (spot check)
-        import torch
-        for im in {id(x): x for x in reqs}.values():
-            x = torch.from_numpy(im.words.view(np.int32)).cuda()
-            y = torch.zeros_like(x)
-            lib_mod.check(lib_mod.me_edges(x, im.w, im.h, im.stride_words, y, 0))
-            torch.cuda.synchronize()
-            if not np.array_equal(y.cpu().numpy().view(np.uint32), outs[id(im)]):
-                result["exact"] = False
-                break
-        else:
-            result["exact"] = True
-        result["stats"] = srv.stats()
+            st0 = srv.stats()
+            r = lib_mod.load_run(srv, reqs, arrival_s=t_arr, clients=open_clients)
+            st1 = srv.stats()
+            result[f"load_{f}"] = dict(offered_req_per_s=round(f * sat_rate, 1),
+                                       **point(r, st0, st1))
+        st = srv.stats()
+        result["stats"] = st
     finally:
         srv.close()
     return result

@@ -133,11 +133,17 @@ int me_edges_staged(const uint32_t *img, int32_t w, int32_t h,
  * the library keeps until the process exits.  Images with
  * h * stride_words > ME_STATIC_MASK_WORDS return ME_ERR_TOO_BIG with nothing
  * enqueued.  The first call on a device looks up the array's device address
- * (no allocation); make that first call before any stream capture.  All
- * calls on a device share the array, so calls whose GPU work may overlap
- * (unordered streams) race and must be serialised by the caller.  Nothing
- * is read from the array before the call has written it.  Other arguments
- * and results as me_edges_staged.
+ * (no allocation by the library); make that first call before any stream
+ * capture.  Under CUDA's lazy module loading (the default) that first call
+ * is also when the driver places the array in device memory, so a caller
+ * whose device memory is capped, or handed to a caching allocator, after
+ * start-up must make one call at start-up, before that happens.  The
+ * address is kept for the life of the process; after a cudaDeviceReset,
+ * call me_shutdown() before the next call so that it is looked up again.
+ * All calls on a device share the array, so calls whose GPU work may
+ * overlap (unordered streams) race and must be serialised by the caller.
+ * Nothing is read from the array before the call has written it.  Other
+ * arguments and results as me_edges_staged.
  */
 #define ME_STATIC_MASK_WORDS 1048576
 int me_edges_staged_static(const uint32_t *img, int32_t w, int32_t h,
@@ -384,7 +390,11 @@ typedef struct me_serve_cfg {
                                    0 = same as hbm_budget_bytes */
     int32_t max_inflight;       /* launched, unfinished batches (>= 1) */
     int32_t max_batch;          /* requests per launch (>= 1) */
-    int32_t tick_us;            /* engine wake-up period when idle */
+    int32_t tick_us;            /* while batches are in flight, the period
+                                   in microseconds at which the completion
+                                   thread checks the oldest one; 0 checks
+                                   continuously (lowest latency, one host
+                                   core busy while the GPU works) */
     int32_t device;             /* CUDA device ordinal */
 } me_serve_cfg;
 
@@ -401,9 +411,13 @@ typedef struct me_server me_server;
  * the HBM budget, keeps their packed images and edge maps resident on the
  * device, and runs whatever is admitted as batches (continuous batching:
  * requests that arrive while batches run join the next launch once memory
- * and an in-flight slot are free).  Copies and kernels overlap on separate
+ * and an in-flight slot are free), and a second thread that retires
+ * finished batches in order.  Copies and kernels overlap on separate
  * streams.  The server owns a device pool of hbm_budget_bytes and a pinned
- * pool of staging_bytes.
+ * pool of staging_bytes, each split into halves for images and edge maps; a
+ * request takes its packed size (rounded up to 256 bytes) in each half.
+ * Requests of a batch that lie next to one another in both pools move
+ * together, one copy each way.
  */
 int me_serve_open(const me_serve_cfg *cfg, me_server **out);
 
@@ -424,7 +438,10 @@ int me_serve_submit(me_server *srv, const uint32_t *host_img, int32_t w,
  * to host_edge (h rows of the request's stride_words, padding written 0)
  * and the timing in *t (may be NULL); ME_PENDING (timeout 0) or
  * ME_TIMEOUT when not ready; ME_ERR_TICKET for an unknown or already
- * collected ticket.  A collected ticket is forgotten.
+ * collected ticket; ME_ERR_ARG if another thread is already waiting for the
+ * same ticket.  A collected ticket is forgotten.  Only the thread waiting
+ * for a request is woken when it completes, so many threads can each wait
+ * for their own requests.
  */
 int me_serve_poll(me_server *srv, uint64_t ticket, uint32_t *host_edge,
                   int64_t timeout_us, me_timing *t);
@@ -432,9 +449,8 @@ int me_serve_poll(me_server *srv, uint64_t ticket, uint32_t *host_edge,
 /*
  * Forget a ticket.  A request still queued is dropped at once; one already
  * on the GPU finishes there and its memory is reclaimed when its batch
- * retires; a finished one is freed.  ME_ERR_TICKET for an unknown ticket.
- * Polling and cancelling the same ticket from two threads at once is not
- * allowed.
+ * retires; a finished one is freed.  ME_ERR_TICKET for an unknown ticket;
+ * ME_ERR_ARG while another thread's me_serve_poll is waiting for it.
  */
 int me_serve_cancel(me_server *srv, uint64_t ticket);
 
@@ -446,10 +462,18 @@ int me_serve_stats(me_server *srv, int64_t *submitted, int64_t *completed,
                    int64_t *batches, int64_t *peak_bytes);
 
 /*
+ * Host-device copies the server has issued since open, both directions
+ * (at most two per request; fewer when neighbouring requests move
+ * together).
+ */
+int me_serve_copies(me_server *srv, int64_t *copies);
+
+/*
  * Stop accepting requests, finish the ones admitted or queued (waiting at
  * most drain_timeout_us; negative = no limit), then free the server.
  * Uncollected results are dropped.  Returns ME_TIMEOUT if the drain ran
  * out (the server is freed all the same once its GPU work has ended).
+ * No other call on the same server may run at the same time or after it.
  */
 int me_serve_close(me_server *srv, int64_t drain_timeout_us);
 
@@ -464,7 +488,8 @@ int me_serve_close(me_server *srv, int64_t drain_timeout_us);
  */
 int me_device_faults(int32_t clear, uint32_t *flags);
 
-/* Free the batch rings, graphs and plans' shared state on every device. */
+/* Free the batch rings, graphs and plans' shared state on every device,
+ * and forget the device addresses me_edges_staged_static has looked up. */
 int me_shutdown(void);
 
 #ifdef __cplusplus

@@ -114,6 +114,7 @@ PROTOTYPES = {
     "me_serve_cancel": (ctypes.c_int, [c_vp, c_u64]),
     "me_serve_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                                       ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
+    "me_serve_copies": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i64)]),
     "me_serve_close": (ctypes.c_int, [c_vp, c_i64]),
     "me_device_faults": (ctypes.c_int, [c_i32, ctypes.POINTER(ctypes.c_uint32)]),
     "me_shutdown": (ctypes.c_int, []),
@@ -342,11 +343,16 @@ class Server:
         return load().me_serve_cancel(self._h, ticket)
 
     def stats(self):
-        v = [c_i64() for _ in range(4)]
-        check(load().me_serve_stats(self._h, *[ctypes.byref(x) for x in v]),
+        v = [c_i64() for _ in range(5)]
+        check(load().me_serve_stats(self._h, *[ctypes.byref(x) for x in v[:4]]),
               "me_serve_stats")
-        return dict(zip(("submitted", "completed", "batches", "peak_bytes"),
+        check(load().me_serve_copies(self._h, ctypes.byref(v[4])), "me_serve_copies")
+        return dict(zip(("submitted", "completed", "batches", "peak_bytes", "copies"),
                         [x.value for x in v]))
+
+    @property
+    def handle(self):
+        return self._h
 
     def close(self, drain_timeout_us=-1) -> int:
         rc = C["ME_OK"]
@@ -360,3 +366,67 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------ serving load generator
+LOADGEN_PATH = os.path.join(PKG, "libme_loadgen.so")
+
+
+class me_load_item(ctypes.Structure):
+    _fields_ = [("img", c_vp), ("expect", c_vp), ("w", c_i32), ("h", c_i32),
+                ("stride_words", c_i32), ("boundary", c_i32)]
+
+
+class me_load_result(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("mismatches", c_i64), ("errors", c_i64),
+                ("first_error", c_i32), ("pad", c_i32)]
+
+
+_loadgen = None
+
+
+def load_loadgen() -> ctypes.CDLL:
+    """libme_loadgen.so (built beside libme.so; raises if missing)."""
+    global _loadgen
+    load()
+    with _lock:
+        if _loadgen is None:
+            if not os.path.exists(LOADGEN_PATH):
+                raise OSError(f"{LOADGEN_PATH} not built: run paper_1401_5245_gb300.build")
+            lg = ctypes.CDLL(LOADGEN_PATH)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lg.me_load_run.restype = ctypes.c_int
+            lg.me_load_run.argtypes = [c_vp, ctypes.POINTER(me_load_item), c_i64, dp, c_i32,
+                                       c_i32, dp, dp, ctypes.POINTER(me_load_result)]
+            _loadgen = lg
+    return _loadgen
+
+
+def load_run(server: "Server", reqs, expect=None, arrival_s=None, clients=4, window=32):
+    """Drive `server` with the requests `reqs` (objects with .words, .w, .h,
+    .stride_words, .boundary) from C threads (me_load_run).  expect: None or
+    one edge-map array per request to compare with.  arrival_s: None for a
+    closed loop of `window` outstanding requests per client, else the
+    arrival times in seconds (open loop).  Returns wall_s, mismatches,
+    errors, first_error and the per-request latency_us / server_us arrays."""
+    import numpy as np
+    n = len(reqs)
+    items = (me_load_item * n)()
+    for i, im in enumerate(reqs):
+        items[i].img = im.words.ctypes.data
+        items[i].expect = expect[i].ctypes.data if expect is not None else None
+        items[i].w, items[i].h = im.w, im.h
+        items[i].stride_words, items[i].boundary = im.stride_words, im.boundary
+    lat = np.full(n, np.nan)
+    srv_us = np.full(n, np.nan)
+    dp = ctypes.POINTER(ctypes.c_double)
+    arr = None
+    if arrival_s is not None:
+        arr = np.ascontiguousarray(np.asarray(arrival_s, dtype=np.float64) * 1e6)
+    res = me_load_result()
+    check(load_loadgen().me_load_run(
+        server.handle, items, n, arr.ctypes.data_as(dp) if arr is not None else None,
+        clients, window, lat.ctypes.data_as(dp), srv_us.ctypes.data_as(dp),
+        ctypes.byref(res)), "me_load_run")
+    return {"wall_s": res.wall_s, "mismatches": res.mismatches, "errors": res.errors,
+            "first_error": res.first_error, "latency_us": lat, "server_us": srv_us}

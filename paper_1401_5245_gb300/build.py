@@ -2,7 +2,9 @@
 
 Each translation unit under csrc/ compiles in parallel into _build/, then
 one link produces paper_1401_5245_gb300/libme.so against the shared CUDA
-runtime (the same libcudart.so.13 torch loads).
+runtime (the same libcudart.so.13 torch loads).  The serving load
+generator (csrc/loadgen/, host code calling libme's C ABI only) becomes
+libme_loadgen.so beside it.
 """
 from __future__ import annotations
 
@@ -19,6 +21,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libme.so")
+LOADGEN_SRC = os.path.join(CSRC, "loadgen", "me_loadgen.cpp")
+LOADGEN = os.path.join(PKG, "libme_loadgen.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -83,7 +87,31 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             raise RuntimeError("link of libme.so failed")
         os.replace(tmp, LIB)
+    build_loadgen(force)
     return LIB
+
+
+def cxx() -> str:
+    for cand in (os.environ.get("CXX"), shutil.which("g++"), shutil.which("c++")):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("no C++ compiler found")
+
+
+def build_loadgen(force: bool = False) -> str:
+    """libme_loadgen.so: host code linked against libme.so (found beside it)."""
+    deps = [LOADGEN_SRC, os.path.join(INCLUDE, "me.h"), LIB]
+    if not (force or _stale(LOADGEN, deps)):
+        return LOADGEN
+    tmp = LOADGEN + f".tmp{os.getpid()}"
+    cmd = [cxx(), "-O2", "-std=c++17", "-shared", "-fPIC", "-Wall", "-I", INCLUDE,
+           LOADGEN_SRC, "-o", tmp, "-L", PKG, "-lme", "-Wl,-rpath,$ORIGIN", "-lpthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
+        raise RuntimeError("build of libme_loadgen.so failed")
+    os.replace(tmp, LOADGEN)
+    return LOADGEN
 
 
 if __name__ == "__main__":

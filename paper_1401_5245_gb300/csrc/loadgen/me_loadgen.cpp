@@ -1,0 +1,176 @@
+// Load generator for the serving engine (libme_loadgen.so).
+//
+// Drives a server through the public C ABI of include/me.h only, from host
+// threads, so that the offered load is bounded by the server and the host
+// link rather than by the client.  Each client is one thread that submits
+// its share of the requests and collects their results oldest first: in a
+// closed loop it keeps up to `window` requests outstanding; in an open loop
+// it submits every request at its scheduled arrival time and, between
+// arrivals, waits for the oldest result no longer than until the next
+// arrival.  Latency is measured from the scheduled arrival (open loop) or
+// from the submit call (closed loop) to the return of the poll that
+// delivered the result, so a client or server that falls behind its
+// schedule shows in it.  Every result can be compared with the edge map it
+// must equal.
+//
+// Not part of libme's C ABI; bench.py and the serving tests load it.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <vector>
+
+#include <sys/prctl.h>
+
+#include "me.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double us_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+// Sleep until t: coarse sleep to 100 us before it, then yield.
+void wait_until(Clock::time_point t) {
+    for (;;) {
+        const auto now = Clock::now();
+        if (now >= t) return;
+        const double left = us_between(now, t);
+        if (left > 150.0)
+            std::this_thread::sleep_for(std::chrono::microseconds((int64_t)(left - 100.0)));
+        else
+            std::this_thread::yield();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+typedef struct me_load_item {
+    const uint32_t *img;       // host image: h rows of stride_words words
+    const uint32_t *expect;    // NULL, or the edge map the result must equal
+    int32_t w, h, stride_words, boundary;
+} me_load_item;
+
+typedef struct me_load_result {
+    double wall_s;             // first submit to last result
+    int64_t mismatches;        // results that differed from expect
+    int64_t errors;            // failed submits or polls
+    int32_t first_error;       // status of the first failure (0: none)
+    int32_t pad;
+} me_load_result;
+
+/*
+ * Run n requests through srv.  Request i goes to client i % clients.
+ * arrival_us: NULL for a closed loop (each client keeps up to `window`
+ * requests outstanding), else the arrival time of each request in
+ * microseconds from the start (open loop; window is ignored).
+ * latency_us[i] (may be NULL): arrival (open) or submit (closed) to result
+ * delivered; server_us[i] (may be NULL): the server's submit-to-ready time
+ * (me_timing.total_us).  Returns ME_OK or ME_ERR_ARG; failures of single
+ * requests are counted in *res.
+ */
+int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
+                const double *arrival_us, int32_t clients, int32_t window,
+                double *latency_us, double *server_us, me_load_result *res) {
+    if (srv == nullptr || items == nullptr || n <= 0 || clients < 1 || res == nullptr ||
+        (arrival_us == nullptr && window < 1))
+        return ME_ERR_ARG;
+    std::memset(res, 0, sizeof(*res));
+    std::atomic<int64_t> mismatches{0}, errors{0};
+    std::atomic<int32_t> first_error{0};
+    auto fail = [&](int rc) {
+        errors.fetch_add(1);
+        int32_t z = 0;
+        first_error.compare_exchange_strong(z, rc);
+    };
+    size_t max_bytes = 0;
+    for (int64_t i = 0; i < n; ++i)
+        max_bytes = std::max(max_bytes, (size_t)items[i].h * (size_t)items[i].stride_words * 4);
+
+    std::atomic<int> ready{0};
+    std::atomic<bool> go{false};
+    Clock::time_point t0;
+    std::vector<Clock::time_point> t_last((size_t)clients);
+    const bool open = arrival_us != nullptr;
+    auto arrival = [&](int64_t i) {
+        return t0 + std::chrono::nanoseconds((int64_t)(arrival_us[i] * 1e3));
+    };
+
+    std::vector<std::thread> th;
+    for (int c = 0; c < clients; ++c) {
+        th.emplace_back([&, c] {
+            std::vector<uint32_t> scratch(max_bytes / 4 + 1);
+            struct Out {
+                int64_t i;
+                uint64_t ticket;
+                Clock::time_point from;
+            };
+            std::deque<Out> out;
+            prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);   // 1 us sleep precision
+            ready.fetch_add(1);
+            while (!go.load(std::memory_order_acquire)) std::this_thread::yield();
+            Clock::time_point last = t0;
+            int64_t next = c;
+            while (next < n || !out.empty()) {
+                const auto now = Clock::now();
+                const bool due = next < n && (open ? arrival(next) <= now
+                                                   : (int)out.size() < window);
+                if (due) {
+                    const me_load_item &it = items[next];
+                    const auto from = open ? arrival(next) : Clock::now();
+                    uint64_t tk = 0;
+                    const int rc = me_serve_submit(srv, it.img, it.w, it.h, it.stride_words,
+                                                   it.boundary, &tk);
+                    if (rc == ME_OK) out.push_back({next, tk, from}); else fail(rc);
+                    next += clients;
+                    continue;
+                }
+                if (out.empty()) {                       // open loop, idle
+                    wait_until(arrival(next));
+                    continue;
+                }
+                // the oldest result, waiting no longer than the next arrival
+                int64_t timeout = -1;
+                if (open && next < n)
+                    timeout = (int64_t)std::max(0.0, us_between(now, arrival(next)));
+                me_timing tm{};
+                const Out o = out.front();
+                const int rc = me_serve_poll(srv, o.ticket, scratch.data(), timeout, &tm);
+                if (rc == ME_PENDING || rc == ME_TIMEOUT) continue;
+                out.pop_front();
+                last = Clock::now();
+                if (rc != ME_OK) {
+                    fail(rc);
+                    continue;
+                }
+                if (latency_us) latency_us[o.i] = us_between(o.from, last);
+                if (server_us) server_us[o.i] = tm.total_us;
+                const me_load_item &it = items[o.i];
+                if (it.expect && std::memcmp(scratch.data(), it.expect,
+                                             (size_t)it.h * (size_t)it.stride_words * 4) != 0)
+                    mismatches.fetch_add(1);
+            }
+            t_last[c] = last;
+        });
+    }
+    while (ready.load() < (int)th.size()) std::this_thread::yield();
+    t0 = Clock::now();
+    go.store(true, std::memory_order_release);
+    for (auto &t : th) t.join();
+    Clock::time_point end = t0;
+    for (auto &t : t_last) end = std::max(end, t);
+    res->wall_s = us_between(t0, end) * 1e-6;
+    res->mismatches = mismatches.load();
+    res->errors = errors.load();
+    res->first_error = first_error.load();
+    return ME_OK;
+}
+
+}  // extern "C"

@@ -310,6 +310,9 @@ class BatchRing {
 // Release the host-batch pipelines (streams, device slots) on every device.
 int host_pipes_shutdown();
 
+// Forget the device addresses me_edges_staged_static has cached.
+void static_forget_all();
+
 // The five staged passes.
 cudaError_t launch_staged(const Geo &g, uint32_t *mask, uint32_t *edge,
                           cudaStream_t s);

@@ -1,20 +1,43 @@
 // Serving engine: continuous batching of edge-map requests on one GPU.
 //
-// submit() copies the request into pinned staging (or, when the staging
-// pool is full, into heap memory until staging frees up) and queues it.  An
-// engine thread admits queued requests in arrival order while the device
-// pool (the HBM budget) has room for the request's packed image and edge
-// map and fewer than max_inflight batches are on the GPU; each admitted
-// group becomes one batch:
+// submit() takes a range of pinned staging (or, when staging is full, heap
+// memory until staging frees up), queues the request and copies the image
+// in.  An engine thread admits queued requests in arrival order while the
+// device pool (the HBM budget) has room for the request's packed image and
+// edge map and fewer than max_inflight batches are on the GPU; each
+// admitted group becomes one batch:
 //     H2D copies (stream h2d) -> persistent batch kernel under a CUDA graph
 //     (stream compute) -> D2H copies (stream d2h) -> completion event.
 // The three streams let the uploads of the next batch and the downloads of
-// the previous one overlap the running kernel.  The engine retires batches
-// in order as their events complete, frees their device memory and wakes
-// pollers; poll() copies a finished edge map out of staging and forgets the
-// ticket.  All waits are bounded by the caller's timeouts or by the engine
-// tick; nothing here spins on the GPU.
+// the previous one overlap the running kernel.  A completion thread watches
+// the oldest batch's event, retires batches in order as they finish, frees
+// their device memory and wakes the pollers of their requests and the
+// engine; poll() copies a finished edge map out of staging and forgets the
+// ticket.
+//
+// Both pools are split in two halves, inputs in the lower and edge maps in
+// the upper, and a request takes the same offset in both halves of a pool.
+// Staging is handed out by next fit at submit and device memory by next fit
+// at admission, both in arrival order, so the requests of a batch usually
+// sit back to back in staging and on the device alike: the engine merges
+// such neighbours into one copy each way (a batch of hundreds of requests
+// moves in a handful of copies instead of two per request).
+//
+// Locks, taken only in this order when nested: qmu (the queue, staging,
+// admission order, the engine's sleep), dev_mu (the device pool, batches in
+// flight, the completion thread's sleep), then one of kShards ticket shards
+// (ticket -> request, a request's completion state, its poller's wake-up).
+// A submit takes qmu and a shard once each; a poll takes a shard and hands
+// the request's staging back through a lock-free list that the next submit
+// (or the engine) empties under qmu.  The engine sleeps only after stating
+// what it waits for (engine_waiting, waits_for) and re-checking it, and
+// every thread that may unblock it bumps wake_seq and then looks at
+// engine_waiting, so no wake-up is lost and none is sent for nothing.
+//
+// All waits are bounded by the caller's timeouts, by `stop`, or by the
+// GPU's own progress; nothing here spins on a flag the GPU sets.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -40,6 +63,7 @@ double us_since(Clock::time_point a, Clock::time_point b) {
 }
 
 constexpr size_t kAlign = 256;
+constexpr int kShards = 16;
 
 enum State { QUEUED, ADMITTED, DONE, FAILED };
 
@@ -47,52 +71,134 @@ struct Req {
     uint64_t ticket = 0;
     int32_t w = 0, h = 0, stride = 0, boundary = 0;
     size_t bytes = 0, span = 0;        // packed size; rounded to kAlign
-    bool pinned = false;               // input is in staging (else in heap)
-    size_t pin_off = 0;                // staging: input at +0, output at +span
+    bool pinned = false;               // input is in staging (else in heap); qmu
+    std::atomic<bool> copied{false};   // the input copy into staging is done
+    Req *next_free = nullptr;          // link in the server's list of freed requests
+    size_t pin_off = 0;                // staging: input at in + off, output at out + off
     std::unique_ptr<uint32_t[]> heap;  // input while staging was full
-    size_t dev_off = 0;                // device pool: input at +0, output at +span
-    State state = QUEUED;
-    bool cancelled = false;
+    size_t dev_off = 0;                // device: input at in + off, output at out + off
+    State state = QUEUED;              // QUEUED->ADMITTED under qmu, then under the shard
+    bool cancelled = false;            // under qmu and the shard
+    // the condition the poller waiting for this request sleeps on (only that
+    // poller is woken when the request's batch retires); under the shard
+    std::condition_variable *waiter = nullptr;
     Clock::time_point t_submit, t_admit, t_done;
 };
 
 struct Batch {
     std::vector<Req *> reqs;
     cudaEvent_t up = nullptr, kern = nullptr, done = nullptr;
+    bool failed = false;               // a CUDA call of its launch failed
 };
+
+struct Shard {
+    std::mutex mu;
+    std::unordered_map<uint64_t, Req *> map;
+};
+
+// Maximal runs of a batch's requests that lie back to back both in staging
+// and on the device; f(first, last).
+template <class F>
+void for_each_run(const std::vector<Req *> &reqs, F &&f) {
+    size_t i = 0;
+    while (i < reqs.size()) {
+        size_t j = i;
+        while (j + 1 < reqs.size() &&
+               reqs[j + 1]->pin_off == reqs[j]->pin_off + reqs[j]->span &&
+               reqs[j + 1]->dev_off == reqs[j]->dev_off + reqs[j]->span)
+            ++j;
+        f(reqs[i], reqs[j]);
+        i = j + 1;
+    }
+}
 
 }  // namespace
 
 struct me_server {
     me_serve_cfg cfg{};
-    char *dev_base = nullptr;
-    char *pin_base = nullptr;
-    RangeAlloc dev_alloc, pin_alloc;
+    char *dev_base = nullptr;          // [inputs | edge maps], dev_half bytes each
+    char *pin_base = nullptr;          // [inputs | edge maps], pin_half bytes each
+    size_t dev_half = 0, pin_half = 0;
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
     std::unique_ptr<BatchRing> ring;
+    std::thread engine, retirer;
 
-    std::mutex mu;
-    std::condition_variable cv_engine, cv_done;
+    // qmu: the queue, staging, closing/stop, the engine's sleep
+    std::mutex qmu;
+    std::condition_variable cv_engine;
     std::deque<Req *> queue;
-    std::unordered_map<uint64_t, Req *> reqs;
+    RangeAlloc pin_alloc;              // offsets within one staging half
+    bool closing = false, stop = false;
+    std::atomic<int> heap_waiting{0};  // queued requests still in heap memory
+    uint64_t next_ticket = 1;
+
+    // the engine's sleep: what it waits for, and a counter every waker bumps
+    std::atomic<bool> engine_waiting{false};
+    std::atomic<Req *> waits_for{nullptr};  // the request whose copy it needs
+    std::atomic<uint64_t> wake_seq{0};
+    // collected requests whose staging is still to be released (under qmu)
+    std::atomic<Req *> freed{nullptr};
+
+    // dev_mu: the device pool, batches in flight, the completion thread's sleep
+    std::mutex dev_mu;
+    std::condition_variable cv_retire;
+    RangeAlloc dev_alloc;              // offsets within one device half
     std::deque<Batch> inflight;
     std::vector<Batch> spare;          // batches whose events can be reused
-    std::thread engine;
-    bool closing = false, stop = false;
-    uint64_t next_ticket = 1;
-    int64_t submitted = 0, completed = 0, batches = 0;
+    bool stop_retirer = false;
+
+    Shard shards[kShards];
+
+    std::atomic<int64_t> submitted{0}, completed{0}, batches{0}, copies{0};
+
+    Shard &shard(uint64_t ticket) { return shards[ticket % kShards]; }
+    char *dev_in(const Req *r) const { return dev_base + r->dev_off; }
+    char *dev_out(const Req *r) const { return dev_base + dev_half + r->dev_off; }
+    char *pin_in(const Req *r) const { return pin_base + r->pin_off; }
+    char *pin_out(const Req *r) const { return pin_base + pin_half + r->pin_off; }
 
     // ------------------------------------------------------------------
-    void free_req(Req *r) {          // caller holds mu
-        if (r->pinned) pin_alloc.release(r->pin_off, 2 * r->span);
+    void free_req(Req *r) {            // caller holds qmu
+        if (r->pinned) pin_alloc.release(r->pin_off, r->span);
         delete r;
     }
 
-    bool new_batch(Batch *b) {
+    // Hand a finished request to the next holder of qmu (no lock taken).
+    void push_freed(Req *r) {
+        Req *h = freed.load(std::memory_order_relaxed);
+        do {
+            r->next_free = h;
+        } while (!freed.compare_exchange_weak(h, r, std::memory_order_release,
+                                              std::memory_order_relaxed));
+    }
+    void drain_freed() {               // caller holds qmu
+        Req *r = freed.exchange(nullptr, std::memory_order_acquire);
+        while (r) {
+            Req *n = r->next_free;
+            free_req(r);
+            r = n;
+        }
+    }
+
+    // Something the engine may wait for has changed.
+    void wake_engine_locked() {        // caller holds qmu
+        wake_seq.fetch_add(1);
+        if (engine_waiting.load()) cv_engine.notify_one();
+    }
+    void wake_engine() {               // caller holds no server lock
+        wake_seq.fetch_add(1);
+        if (engine_waiting.load()) {
+            std::lock_guard<std::mutex> lk(qmu);
+            cv_engine.notify_one();
+        }
+    }
+
+    bool new_batch(Batch *b) {         // caller holds dev_mu
         if (!spare.empty()) {
-            *b = spare.back();
+            *b = std::move(spare.back());
             spare.pop_back();
             b->reqs.clear();
+            b->failed = false;
             return true;
         }
         const unsigned f = cudaEventDisableTiming;
@@ -105,58 +211,55 @@ struct me_server {
         return true;
     }
 
-    // Retire finished batches (in order); caller holds mu.
-    void retire() {
-        bool any = false;
-        while (!inflight.empty()) {
-            Batch &b = inflight.front();
-            const cudaError_t q = cudaEventQuery(b.done);
-            if (q == cudaErrorNotReady) break;
-            const State st = q == cudaSuccess ? DONE : FAILED;
-            if (q != cudaSuccess) cudaGetLastError();
-            const auto now = Clock::now();
-            for (Req *r : b.reqs) {
-                dev_alloc.release(r->dev_off, 2 * r->span);
-                r->t_done = now;
-                r->state = st;
-                ++completed;
-                if (r->cancelled) free_req(r);
-            }
-            b.reqs.clear();
-            spare.push_back(std::move(b));
-            inflight.pop_front();
-            any = true;
-        }
-        if (any) cv_done.notify_all();
-    }
-
     // Give staging to queued requests still held in heap memory, in order.
-    void stage_heap_requests() {
+    // Called with qmu held through lk; the copies run with it released (the
+    // requests are not admitted meanwhile: copied is false).
+    void stage_heap_requests(std::unique_lock<std::mutex> &lk) {
+        if (heap_waiting.load() == 0) return;
+        std::vector<Req *> moved;
         for (Req *r : queue) {
             if (r->pinned) continue;
             size_t off;
-            if (!pin_alloc.alloc(2 * r->span, &off)) break;
-            std::memcpy(pin_base + off, r->heap.get(), r->bytes);
-            r->heap.reset();
+            if (!pin_alloc.alloc_next(r->span, &off)) break;
             r->pin_off = off;
             r->pinned = true;
+            r->copied = false;
+            --heap_waiting;
+            moved.push_back(r);
+        }
+        if (moved.empty()) return;
+        lk.unlock();
+        for (Req *r : moved) {
+            std::memcpy(pin_in(r), r->heap.get(), r->bytes);
+            r->heap.reset();
+        }
+        lk.lock();
+        // requests cancelled (or dropped by close) during the copy are
+        // freed here, by the thread that held them
+        for (Req *r : moved) {
+            if (r->cancelled) free_req(r);
+            else r->copied.store(true);
         }
     }
 
-    // Issue one admitted batch; called without mu.
-    void launch(Batch &b) {
+    // Issue one admitted batch; called without locks.  Returns false if any
+    // CUDA call failed (the done event is still recorded behind whatever
+    // was enqueued).
+    bool launch(Batch &b, int64_t *ncopies) {
         cudaError_t e = cudaSuccess;
+        int64_t nc = 0;
         std::vector<me_desc> descs;
         descs.reserve(b.reqs.size());
-        for (Req *r : b.reqs) {
-            char *din = dev_base + r->dev_off;
+        for_each_run(b.reqs, [&](const Req *a, const Req *z) {
+            const size_t n = z->pin_off + z->bytes - a->pin_off;
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(din, pin_base + r->pin_off, r->bytes,
-                                    cudaMemcpyHostToDevice, s_h2d);
-            descs.push_back({reinterpret_cast<const uint32_t *>(din),
-                             reinterpret_cast<uint32_t *>(din + r->span), r->w, r->h, r->stride,
+                e = cudaMemcpyAsync(dev_in(a), pin_in(a), n, cudaMemcpyHostToDevice, s_h2d);
+            ++nc;
+        });
+        for (Req *r : b.reqs)
+            descs.push_back({reinterpret_cast<const uint32_t *>(dev_in(r)),
+                             reinterpret_cast<uint32_t *>(dev_out(r)), r->w, r->h, r->stride,
                              r->boundary});
-        }
         if (e == cudaSuccess) e = cudaEventRecord(b.up, s_h2d);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s_comp, b.up, 0);
         if (e == cudaSuccess) {
@@ -165,82 +268,143 @@ struct me_server {
         }
         if (e == cudaSuccess) e = cudaEventRecord(b.kern, s_comp);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s_d2h, b.kern, 0);
-        for (Req *r : b.reqs)
+        for_each_run(b.reqs, [&](const Req *a, const Req *z) {
+            const size_t n = z->pin_off + z->bytes - a->pin_off;
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(pin_base + r->pin_off + r->span,
-                                    dev_base + r->dev_off + r->span, r->bytes,
-                                    cudaMemcpyDeviceToHost, s_d2h);
-        // the done event is recorded even after a failure so that the batch
-        // retires once whatever was enqueued has finished
-        cudaError_t f = cudaEventRecord(b.done, s_d2h);
+                e = cudaMemcpyAsync(pin_out(a), dev_out(a), n, cudaMemcpyDeviceToHost, s_d2h);
+            ++nc;
+        });
+        // recorded even after a failure, so that the batch retires once
+        // whatever was enqueued has finished
+        const cudaError_t f = cudaEventRecord(b.done, s_d2h);
+        *ncopies = nc;
         if (e != cudaSuccess || f != cudaSuccess) {
             cudaGetLastError();
-            std::lock_guard<std::mutex> lk(mu);
-            failed_launch = true;              // run() fails the batch's requests
+            return false;
         }
+        return true;
     }
-    bool failed_launch = false;
 
-    void run() {
+    // Engine thread: admission and launches.
+    enum Blocked { NOTHING, EMPTY, NOT_COPIED, HEAP, NO_SLOT, NO_MEMORY };
+
+    // Admit a batch from the head of the queue into b (caller holds qmu).
+    Blocked admit(Batch *b) {
+        if (queue.empty()) return EMPTY;
+        Req *f = queue.front();
+        if (!f->pinned) return HEAP;
+        if (!f->copied.load()) return NOT_COPIED;
+        std::lock_guard<std::mutex> dl(dev_mu);
+        if ((int)inflight.size() >= cfg.max_inflight) return NO_SLOT;
+        if (!new_batch(b)) return NO_SLOT;
+        const auto now = Clock::now();
+        while (!queue.empty() && (int)b->reqs.size() < cfg.max_batch) {
+            Req *r = queue.front();
+            if (!r->pinned || !r->copied.load()) break;
+            size_t off;
+            if (!dev_alloc.alloc_next(r->span, &off)) break;   // wait for memory
+            r->dev_off = off;
+            r->state = ADMITTED;
+            r->t_admit = now;
+            queue.pop_front();
+            b->reqs.push_back(r);
+        }
+        if (b->reqs.empty()) {
+            spare.push_back(std::move(*b));
+            return NO_MEMORY;
+        }
+        return NOTHING;
+    }
+
+    void run_engine() {
         cudaSetDevice(cfg.device);
-        std::unique_lock<std::mutex> lk(mu);
+        std::unique_lock<std::mutex> lk(qmu);
         for (;;) {
-            retire();
-            stage_heap_requests();
+            const uint64_t seq = wake_seq.load();
+            drain_freed();
+            stage_heap_requests(lk);
+            if (stop) break;
             Batch b;
-            bool have = false;
-            if (!stop && (int)inflight.size() < cfg.max_inflight && !queue.empty() &&
-                queue.front()->pinned) {
-                if (!new_batch(&b)) break;
-                have = true;
-                const auto now = Clock::now();
-                while (!queue.empty() && (int)b.reqs.size() < cfg.max_batch) {
-                    Req *r = queue.front();
-                    if (!r->pinned) break;
-                    size_t off;
-                    if (!dev_alloc.alloc(2 * r->span, &off)) break;   // wait for memory
-                    r->dev_off = off;
-                    r->state = ADMITTED;
-                    r->t_admit = now;
-                    queue.pop_front();
-                    b.reqs.push_back(r);
-                }
-                if (b.reqs.empty()) {
-                    spare.push_back(std::move(b));
-                    have = false;
-                }
-            }
-            if (have) {
+            const Blocked why = admit(&b);
+            if (why == NOTHING) {
                 lk.unlock();
-                launch(b);
-                lk.lock();
-                if (failed_launch) {
-                    // keep the requests failed: their copies or kernel never ran
-                    failed_launch = false;
-                    cudaEventSynchronize(b.done);
-                    cudaGetLastError();
-                    const auto now = Clock::now();
-                    for (Req *r : b.reqs) {
-                        dev_alloc.release(r->dev_off, 2 * r->span);
-                        r->t_done = now;
-                        r->state = FAILED;
-                        ++completed;
-                        if (r->cancelled) free_req(r);
-                    }
-                    b.reqs.clear();
-                    spare.push_back(std::move(b));
-                    cv_done.notify_all();
-                } else {
+                int64_t nc = 0;
+                const bool ok = launch(b, &nc);
+                if (!ok) cudaEventSynchronize(b.done);   // let enqueued work end
+                copies += nc;
+                ++batches;
+                {
+                    // a batch whose copies or kernel never ran: its requests
+                    // fail, in order, once the batches before it have retired
+                    std::lock_guard<std::mutex> dl(dev_mu);
+                    b.failed = !ok;
                     inflight.push_back(std::move(b));
-                    ++batches;
+                    cv_retire.notify_one();
                 }
+                lk.lock();
                 continue;
             }
-            if (stop && inflight.empty()) break;
-            if (!inflight.empty())
-                cv_engine.wait_for(lk, std::chrono::microseconds(std::max(1, cfg.tick_us)));
-            else
-                cv_engine.wait_for(lk, std::chrono::milliseconds(50));
+            // state what is awaited, then look again: a waker changes its
+            // state first and reads engine_waiting / waits_for after
+            Req *f = why == NOT_COPIED ? queue.front() : nullptr;
+            waits_for.store(f);
+            engine_waiting.store(true);
+            const bool changed = wake_seq.load() != seq || (f && f->copied.load());
+            if (!changed) cv_engine.wait_for(lk, std::chrono::milliseconds(20));
+            engine_waiting.store(false);
+            waits_for.store(nullptr);
+        }
+    }
+
+    // Completion thread: retires batches in order as their events complete.
+    // While batches are in flight it queries the oldest one's event every
+    // tick_us microseconds (0: continuously, yielding between queries).
+    void run_retirer() {
+        cudaSetDevice(cfg.device);
+        std::vector<Req *> reqs, gone;
+        for (;;) {
+            cudaEvent_t ev;
+            {
+                std::unique_lock<std::mutex> dl(dev_mu);
+                while (inflight.empty()) {
+                    if (stop_retirer) return;
+                    cv_retire.wait_for(dl, std::chrono::milliseconds(20));
+                }
+                ev = inflight.front().done;
+            }
+            cudaError_t q = cudaEventQuery(ev);
+            while (q == cudaErrorNotReady) {
+                if (cfg.tick_us > 0)
+                    std::this_thread::sleep_for(std::chrono::microseconds(cfg.tick_us));
+                else
+                    std::this_thread::yield();
+                q = cudaEventQuery(ev);
+            }
+            if (q != cudaSuccess) cudaGetLastError();
+            {
+                std::lock_guard<std::mutex> dl(dev_mu);
+                Batch &b = inflight.front();
+                if (b.failed) q = cudaErrorLaunchFailure;
+                for (Req *r : b.reqs) dev_alloc.release(r->dev_off, r->span);
+                reqs.swap(b.reqs);
+                spare.push_back(std::move(b));
+                inflight.pop_front();
+            }
+            const State st = q == cudaSuccess ? DONE : FAILED;
+            const auto now = Clock::now();
+            gone.clear();
+            for (Req *r : reqs) {
+                Shard &sh = shard(r->ticket);
+                std::lock_guard<std::mutex> sl(sh.mu);
+                r->t_done = now;
+                r->state = st;
+                if (r->waiter) r->waiter->notify_one();
+                if (r->cancelled) gone.push_back(r);
+            }
+            completed += (int64_t)reqs.size();
+            reqs.clear();
+            for (Req *r : gone) push_freed(r);
+            wake_engine();                  // a slot and device memory are free
         }
     }
 };
@@ -253,7 +417,14 @@ void destroy(me_server *s) {
     cudaSetDevice(s->cfg.device);
     for (cudaStream_t st : {s->s_h2d, s->s_comp, s->s_d2h})
         if (st) cudaStreamSynchronize(st);
-    for (auto &b : s->inflight) s->spare.push_back(b);
+    for (auto &b : s->inflight) {
+        // admitted requests that were cancelled live only in their batch
+        for (Req *r : b.reqs)
+            if (r->cancelled) delete r;
+        b.reqs.clear();
+        s->spare.push_back(std::move(b));
+    }
+    s->inflight.clear();
     for (auto &b : s->spare) {
         if (b.up) cudaEventDestroy(b.up);
         if (b.kern) cudaEventDestroy(b.kern);
@@ -262,7 +433,13 @@ void destroy(me_server *s) {
     s->ring.reset();
     for (cudaStream_t st : {s->s_h2d, s->s_comp, s->s_d2h})
         if (st) cudaStreamDestroy(st);
-    for (auto &kv : s->reqs) delete kv.second;
+    for (auto &sh : s->shards)
+        for (auto &kv : sh.map) delete kv.second;
+    for (Req *r = s->freed.exchange(nullptr); r != nullptr;) {
+        Req *n = r->next_free;
+        delete r;
+        r = n;
+    }
     if (s->dev_base) cudaFree(s->dev_base);
     if (s->pin_base) cudaFreeHost(s->pin_base);
     cudaGetLastError();
@@ -294,15 +471,23 @@ int me_serve_open(const me_serve_cfg *cfg, me_server **out) {
         return record_cuda(e);
     }
     if (cfg->device >= ndev) return ME_ERR_ARG;
+    // each pool in two halves of whole kAlign units
+    const size_t budget = (size_t)cfg->hbm_budget_bytes / (2 * kAlign) * (2 * kAlign);
+    const size_t staging0 = cfg->staging_bytes > 0 ? (size_t)cfg->staging_bytes : budget;
+    const size_t staging = staging0 / (2 * kAlign) * (2 * kAlign);
+    if (budget == 0 || staging == 0) return ME_ERR_ARG;
     int cur = 0;
     cudaGetDevice(&cur);
     if ((e = cudaSetDevice(cfg->device)) != cudaSuccess) return record_cuda(e);
 
     me_server *s = new (std::nothrow) me_server();
-    if (!s) return ME_ERR_NOMEM;
+    if (!s) {
+        cudaSetDevice(cur);
+        return ME_ERR_NOMEM;
+    }
     s->cfg = *cfg;
-    const size_t budget = (size_t)cfg->hbm_budget_bytes;
-    const size_t staging = cfg->staging_bytes > 0 ? (size_t)cfg->staging_bytes : budget;
+    s->dev_half = budget / 2;
+    s->pin_half = staging / 2;
     if ((e = cudaMalloc(&s->dev_base, budget)) != cudaSuccess) {
         s->dev_base = nullptr;
         return fail_open(s, e, cur);
@@ -311,15 +496,28 @@ int me_serve_open(const me_serve_cfg *cfg, me_server **out) {
         s->pin_base = nullptr;
         return fail_open(s, e, cur);
     }
-    s->dev_alloc.reset(budget, kAlign);
-    s->pin_alloc.reset(staging, kAlign);
+    s->dev_alloc.reset(s->dev_half, kAlign);
+    s->pin_alloc.reset(s->pin_half, kAlign);
     for (cudaStream_t *st : {&s->s_h2d, &s->s_comp, &s->s_d2h})
         if ((e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking)) != cudaSuccess)
             return fail_open(s, e, cur);
     s->ring.reset(new BatchRing(cfg->max_inflight + 1));
     try {
-        s->engine = std::thread([s] { s->run(); });
+        s->engine = std::thread([s] { s->run_engine(); });
+        s->retirer = std::thread([s] { s->run_retirer(); });
     } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->qmu);
+            s->stop = true;
+        }
+        {
+            std::lock_guard<std::mutex> dl(s->dev_mu);
+            s->stop_retirer = true;
+        }
+        s->cv_engine.notify_all();
+        s->cv_retire.notify_all();
+        if (s->engine.joinable()) s->engine.join();
+        if (s->retirer.joinable()) s->retirer.join();
         destroy(s);
         cudaSetDevice(cur);
         return ME_ERR_NOMEM;
@@ -344,100 +542,133 @@ int me_serve_submit(me_server *s, const uint32_t *host_img, int32_t w, int32_t h
     r->bytes = (size_t)h * (size_t)stride_words * 4;
     r->span = (r->bytes + kAlign - 1) / kAlign * kAlign;
     r->t_submit = Clock::now();
+    Req *p = r.get();
     {
-        std::lock_guard<std::mutex> lk(s->mu);
+        std::lock_guard<std::mutex> lk(s->qmu);
         if (s->closing) return ME_ERR_CLOSED;
-        if (2 * r->span > s->dev_alloc.capacity() || 2 * r->span > s->pin_alloc.capacity())
-            return ME_ERR_BUDGET;
-        r->pinned = s->pin_alloc.alloc(2 * r->span, &r->pin_off);
+        if (p->span > s->dev_half || p->span > s->pin_half) return ME_ERR_BUDGET;
+        s->drain_freed();
+        p->pinned = s->pin_alloc.alloc_next(p->span, &p->pin_off);
+        p->ticket = s->next_ticket++;
+        if (p->pinned) {
+            // queued at once, in staging order, but not admitted before the
+            // copy below has finished (copied == false); an engine asleep on
+            // an empty queue now waits for this request's copy
+            s->queue.push_back(p);
+            if (s->queue.size() == 1 && s->engine_waiting.load()) s->waits_for.store(p);
+        }
     }
-    // copy the image while the request is not yet visible to the engine
-    if (r->pinned) {
-        std::memcpy(s->pin_base + r->pin_off, host_img, r->bytes);
-    } else {
-        r->heap.reset(new (std::nothrow) uint32_t[r->bytes / 4]);
-        if (!r->heap) return ME_ERR_NOMEM;
-        std::memcpy(r->heap.get(), host_img, r->bytes);
+    if (!p->pinned) {
+        p->heap.reset(new (std::nothrow) uint32_t[p->bytes / 4]);
+        if (!p->heap) return ME_ERR_NOMEM;      // p was never queued
+        std::memcpy(p->heap.get(), host_img, p->bytes);
     }
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->closing) {
-        s->free_req(r.release());
-        return ME_ERR_CLOSED;
+    {
+        Shard &sh = s->shard(p->ticket);
+        std::lock_guard<std::mutex> sl(sh.mu);
+        sh.map[p->ticket] = p;
     }
-    Req *p = r.release();
-    p->ticket = s->next_ticket++;
-    s->reqs[p->ticket] = p;
-    s->queue.push_back(p);
-    ++s->submitted;
+    r.release();
     *ticket = p->ticket;
-    s->cv_engine.notify_one();
+    ++s->submitted;
+    if (p->pinned) {
+        std::memcpy(s->pin_in(p), host_img, p->bytes);
+        p->copied.store(true);
+        if (s->waits_for.load() == p) s->wake_engine();
+        return ME_OK;
+    }
+    std::lock_guard<std::mutex> lk(s->qmu);
+    p->copied.store(true);
+    s->queue.push_back(p);
+    ++s->heap_waiting;
+    s->wake_engine_locked();
     return ME_OK;
 }
 
 int me_serve_poll(me_server *s, uint64_t ticket, uint32_t *host_edge, int64_t timeout_us,
                   me_timing *t) {
     if (s == nullptr || host_edge == nullptr) return ME_ERR_ARG;
-    std::unique_lock<std::mutex> lk(s->mu);
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) return ME_ERR_TICKET;
+    Shard &sh = s->shard(ticket);
+    std::unique_lock<std::mutex> sl(sh.mu);
+    auto it = sh.map.find(ticket);
+    if (it == sh.map.end()) return ME_ERR_TICKET;
     Req *r = it->second;
     auto ready = [r] { return r->state == DONE || r->state == FAILED; };
     if (!ready()) {
         if (timeout_us == 0) return ME_PENDING;
-        if (timeout_us < 0) {
-            s->cv_done.wait(lk, ready);
-        } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) {
-            return ME_TIMEOUT;
+        if (r->waiter != nullptr) return ME_ERR_ARG;      // another thread polls it
+        std::condition_variable cv;
+        r->waiter = &cv;
+        bool ok = true;
+        if (timeout_us < 0)
+            cv.wait(sl, ready);
+        else
+            ok = cv.wait_for(sl, std::chrono::microseconds(timeout_us), ready);
+        r->waiter = nullptr;
+        if (!ok) return ME_TIMEOUT;
+        it = sh.map.find(ticket);           // the map may have rehashed meanwhile
+    }
+    sh.map.erase(it);
+    sl.unlock();
+    const bool ok = r->state == DONE;
+    if (ok) {
+        std::memcpy(host_edge, s->pin_out(r), r->bytes);
+        if (t) {
+            t->queue_us = us_since(r->t_submit, r->t_admit);
+            t->device_us = us_since(r->t_admit, r->t_done);
+            t->total_us = us_since(r->t_submit, r->t_done);
         }
-        // the request may have been collected or cancelled by another thread
-        it = s->reqs.find(ticket);
-        if (it == s->reqs.end() || it->second != r) return ME_ERR_TICKET;
     }
-    s->reqs.erase(it);
-    if (r->state == FAILED) {
-        s->free_req(r);
-        return ME_ERR_CUDA;
-    }
-    lk.unlock();
-    std::memcpy(host_edge, s->pin_base + r->pin_off + r->span, r->bytes);
-    if (t) {
-        t->queue_us = us_since(r->t_submit, r->t_admit);
-        t->device_us = us_since(r->t_admit, r->t_done);
-        t->total_us = us_since(r->t_submit, r->t_done);
-    }
-    lk.lock();
-    s->free_req(r);
-    s->cv_engine.notify_one();           // staging freed: queued requests may move in
-    return ME_OK;
+    // its staging goes back at the next submit or engine round; requests
+    // waiting in heap memory need the engine to take it
+    s->push_freed(r);
+    if (s->heap_waiting.load() > 0) s->wake_engine();
+    return ok ? ME_OK : ME_ERR_CUDA;
 }
 
 int me_serve_cancel(me_server *s, uint64_t ticket) {
     if (s == nullptr) return ME_ERR_ARG;
-    std::lock_guard<std::mutex> lk(s->mu);
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) return ME_ERR_TICKET;
+    std::lock_guard<std::mutex> lk(s->qmu);
+    Shard &sh = s->shard(ticket);
+    std::lock_guard<std::mutex> sl(sh.mu);
+    auto it = sh.map.find(ticket);
+    if (it == sh.map.end()) return ME_ERR_TICKET;
     Req *r = it->second;
-    s->reqs.erase(it);
+    if (r->waiter != nullptr) return ME_ERR_ARG;   // a poll is waiting for it
+    sh.map.erase(it);
     if (r->state == QUEUED) {
         s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
-        s->free_req(r);
+        if (!r->copied.load()) {
+            r->cancelled = true;            // the engine is copying it in; it frees it
+        } else {
+            if (!r->pinned) --s->heap_waiting;
+            s->free_req(r);
+        }
     } else if (r->state == ADMITTED) {
         r->cancelled = true;                // freed when its batch retires
     } else {
         s->free_req(r);
     }
-    s->cv_engine.notify_one();
+    s->wake_engine_locked();
     return ME_OK;
 }
 
 int me_serve_stats(me_server *s, int64_t *submitted, int64_t *completed, int64_t *batches,
                    int64_t *peak_bytes) {
     if (s == nullptr) return ME_ERR_ARG;
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (submitted) *submitted = s->submitted;
-    if (completed) *completed = s->completed;
-    if (batches) *batches = s->batches;
-    if (peak_bytes) *peak_bytes = (int64_t)s->dev_alloc.peak();
+    if (submitted) *submitted = s->submitted.load();
+    if (completed) *completed = s->completed.load();
+    if (batches) *batches = s->batches.load();
+    if (peak_bytes) {
+        std::lock_guard<std::mutex> dl(s->dev_mu);
+        *peak_bytes = 2 * (int64_t)s->dev_alloc.peak();
+    }
+    return ME_OK;
+}
+
+int me_serve_copies(me_server *s, int64_t *copies) {
+    if (s == nullptr || copies == nullptr) return ME_ERR_ARG;
+    *copies = s->copies.load();
     return ME_OK;
 }
 
@@ -445,38 +676,70 @@ int me_serve_close(me_server *s, int64_t drain_timeout_us) {
     if (s == nullptr) return ME_ERR_ARG;
     int rc = ME_OK;
     {
-        std::unique_lock<std::mutex> lk(s->mu);
+        std::lock_guard<std::mutex> lk(s->qmu);
         s->closing = true;
-        // uncollected results are dropped now, so their staging can take
-        // requests still waiting in heap memory
-        for (auto it = s->reqs.begin(); it != s->reqs.end();) {
+        s->wake_engine_locked();
+    }
+    // uncollected results are dropped now, so their staging can take
+    // requests still waiting in heap memory
+    std::vector<Req *> dropped;
+    for (auto &sh : s->shards) {
+        std::lock_guard<std::mutex> sl(sh.mu);
+        for (auto it = sh.map.begin(); it != sh.map.end();) {
             if (it->second->state == DONE || it->second->state == FAILED) {
-                s->free_req(it->second);
-                it = s->reqs.erase(it);
+                dropped.push_back(it->second);
+                it = sh.map.erase(it);
             } else {
                 ++it;
             }
         }
-        auto drained = [s] { return s->queue.empty() && s->inflight.empty(); };
-        s->cv_engine.notify_one();
-        if (drain_timeout_us < 0) {
-            while (!drained()) s->cv_done.wait_for(lk, std::chrono::milliseconds(10));
-        } else {
-            const auto until = Clock::now() + std::chrono::microseconds(drain_timeout_us);
-            while (!drained() && Clock::now() < until)
-                s->cv_done.wait_for(lk, std::chrono::milliseconds(1));
-            if (!drained()) rc = ME_TIMEOUT;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->qmu);
+        for (Req *r : dropped) s->free_req(r);
+        s->wake_engine_locked();
+    }
+    auto drained = [s] {
+        std::lock_guard<std::mutex> lk(s->qmu);
+        std::lock_guard<std::mutex> dl(s->dev_mu);
+        return s->queue.empty() && s->inflight.empty();
+    };
+    const auto until = Clock::now() + std::chrono::microseconds(drain_timeout_us);
+    while (!drained()) {
+        if (drain_timeout_us >= 0 && Clock::now() >= until) {
+            rc = ME_TIMEOUT;
+            break;
         }
-        // requests never admitted are dropped
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    {
+        // requests never admitted are dropped (one the engine is copying
+        // into staging is freed by the engine when the copy is done)
+        std::lock_guard<std::mutex> lk(s->qmu);
         for (Req *r : s->queue) {
-            s->reqs.erase(r->ticket);
-            s->free_req(r);
+            Shard &sh = s->shard(r->ticket);
+            {
+                std::lock_guard<std::mutex> sl(sh.mu);
+                sh.map.erase(r->ticket);
+            }
+            if (!r->copied.load()) r->cancelled = true;
+            else s->free_req(r);
         }
         s->queue.clear();
+        s->heap_waiting.store(0);
         s->stop = true;
-        s->cv_engine.notify_one();
+        s->wake_seq.fetch_add(1);
+        s->cv_engine.notify_all();
     }
     if (s->engine.joinable()) s->engine.join();
+    {
+        // the engine has launched its last batch; the completion thread
+        // retires what is in flight and then stops
+        std::lock_guard<std::mutex> dl(s->dev_mu);
+        s->stop_retirer = true;
+        s->cv_retire.notify_all();
+    }
+    if (s->retirer.joinable()) s->retirer.join();
     destroy(s);
     return rc;
 }

@@ -5,11 +5,18 @@
 //
 // The array belongs to the library's CUDA module: every GPU that loads the
 // library holds kStaticMaskWords * 4 bytes for it until the process exits.
+// With CUDA's lazy module loading (the default) the driver places the module,
+// and so the array, in device memory only when it is first used, which is
+// the address lookup below: the first call on a device is therefore where
+// the 4 MiB is taken, and a caller whose device memory is capped or handed
+// to a caching allocator later must make that first call before then.
 // In host code the name g_static_mask is only a host-side stand-in, never a
 // device address, so its device address is looked up once per device with
 // cudaGetSymbolAddress (on the first call with that device current) and
-// cached.  Every call on a device shares the one array: it is fully
-// rewritten by pass 1 before passes 2-5 read it, so nothing left by an
+// cached.  A device reset (cudaDeviceReset) reloads the module, possibly
+// elsewhere, so me_shutdown() forgets the cached addresses and the next call
+// looks them up again.  Every call on a device shares the one array: it is
+// fully rewritten by pass 1 before passes 2-5 read it, so nothing left by an
 // earlier call is ever read, but two calls whose work overlaps on the GPU
 // (different streams, no ordering between them) race on it.
 #include <mutex>
@@ -45,6 +52,13 @@ static int static_mask_ptr(uint32_t **out) {
     }
     *out = g_static_ptr[dev];
     return ME_OK;
+}
+
+// Forget every cached address (me_shutdown): after a device reset the next
+// call looks the array up again in the reloaded module.
+void static_forget_all() {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    for (auto &p : g_static_ptr) p = nullptr;
 }
 
 }  // namespace me

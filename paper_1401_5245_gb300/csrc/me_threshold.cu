@@ -374,7 +374,8 @@ int thr_setup(const uint8_t *grey, int32_t w, int32_t h, int32_t pitch_bytes, ui
     g->pitch = pitch_bytes;
     g->stride = stride_words;
     g->nw = (int32_t)(((int64_t)w + 31) / 32);
-    g->ncb = (stride_words + kWideLanes - 1) / kWideLanes;
+    // in 64 bits: stride_words + 29 overflows int32 for the widest strides
+    g->ncb = (int32_t)(((int64_t)stride_words + kWideLanes - 1) / kWideLanes);
     g->lastmask = (w & 31) ? ((1u << (w & 31)) - 1u) : kAllOnes;
     g->fill = boundary == ME_BOUNDARY_WHITE ? kAllOnes : 0u;
     g->t4 = 0;
@@ -392,7 +393,7 @@ int thr_grid(const void *fn, TGeo *g, int *ntasks, unsigned *grid) {
     if ((rc = cached_occupancy(fn, 32 * kThrWarps, 0, &occ)) != ME_OK) return rc;
     const int64_t resident = (int64_t)std::max(1, occ) * di.sm_count * kThrWarps;
     g->band = threshold_band(g->ncb, g->h, resident);
-    const int64_t n = (int64_t)g->ncb * ((g->h + g->band - 1) / g->band);
+    const int64_t n = (int64_t)g->ncb * (((int64_t)g->h + g->band - 1) / g->band);
     if (n > INT32_MAX) return ME_ERR_ARG;
     *ntasks = (int)n;
     *grid = (unsigned)std::max<int64_t>(1, (std::min(n, resident) + kThrWarps - 1) / kThrWarps);

@@ -2,6 +2,7 @@
 under concurrent submitters, a budget small enough to force queuing, heap
 fallback when staging is full, cancellation, timeouts and budget refusal.
 All failures are made on the host (no GPU fault is ever provoked)."""
+import ctypes
 import threading
 
 import numpy as np
@@ -91,10 +92,11 @@ def test_served_equals_alone_with_concurrent_submitters(pool):
         assert st["batches"] >= 1 and 0 < st["peak_bytes"] <= 256 << 20
     finally:
         assert srv.close() == 0
-    # and the alone result is the oracle's
-    for im in pool[:10]:
+    # every served shape (glyphs, crops, pages, odd shapes, black boundary)
+    # is also the oracle's edge map
+    for im in pool:
         want = O.edges(S.unpack(im.words, im.w), im.boundary)
-        assert np.array_equal(S.unpack(refs[id(im)], im.w), want)
+        assert np.array_equal(S.unpack(refs[id(im)], im.w), want), (im.w, im.h)
 
 
 def test_small_budget_forces_queueing(pool):
@@ -179,3 +181,68 @@ def test_close_drops_uncollected_and_bad_args(pool):
     h = _lib.c_vp()
     import ctypes
     assert L.me_serve_open(ctypes.byref(cfg), ctypes.byref(h)) == _lib.C["ME_ERR_ARG"]
+
+
+# ------------------------------------------------- the C load generator
+def oracle_words(im):
+    """The oracle's edge map of a pool image, packed in the image's layout."""
+    e = O.edges(S.unpack(im.words, im.w), im.boundary)
+    return S.pack(e, im.stride_words)
+
+
+def test_load_generator_closed_loop_every_result_is_the_oracles(pool):
+    """Many clients in a closed loop through the C load generator: every
+    result equals the oracle's edge map, requests share launches (continuous
+    batching) and neighbouring requests share copies."""
+    want = {id(im): oracle_words(im) for im in pool}
+    g = np.random.default_rng(5)
+    reqs = [pool[int(i)] for i in g.integers(0, len(pool), 3000)]
+    srv = _lib.Server(hbm_budget_bytes=1 << 30, staging_bytes=512 << 20, max_inflight=1,
+                      max_batch=512, tick_us=0)
+    try:
+        r = _lib.load_run(srv, reqs, expect=[want[id(im)] for im in reqs], clients=4,
+                          window=32)
+        st = srv.stats()
+    finally:
+        assert srv.close() == 0
+    assert r["errors"] == 0 and r["first_error"] == 0
+    assert r["mismatches"] == 0
+    assert st["completed"] == len(reqs)
+    assert not np.isnan(r["latency_us"]).any()
+    assert (r["server_us"] <= r["latency_us"] + 1e-3).all()
+    # one batch on the GPU at a time and 128 requests outstanding: the
+    # requests that arrive meanwhile share the next launch
+    assert st["completed"] / st["batches"] > 2, st
+    # copies: far fewer than two per request
+    assert st["copies"] < st["completed"], st
+
+
+def test_load_generator_open_loop_and_black_boundary(pool):
+    """Poisson arrivals (open loop) with black-boundary requests mixed in:
+    every result is the oracle's and the latencies are measured from the
+    scheduled arrivals."""
+    items = []
+    for im in pool:
+        items.append(im)
+        items.append(S.Image(im.words, im.w, im.h, 1 - im.boundary))
+    want = {id(im): oracle_words(im) for im in items}
+    g = np.random.default_rng(6)
+    reqs = [items[int(i)] for i in g.integers(0, len(items), 600)]
+    t = np.cumsum(g.exponential(1 / 20000.0, len(reqs)))
+    srv = _lib.Server(hbm_budget_bytes=256 << 20, staging_bytes=256 << 20, max_inflight=2,
+                      max_batch=64, tick_us=0)
+    try:
+        r = _lib.load_run(srv, reqs, expect=[want[id(im)] for im in reqs], arrival_s=t,
+                          clients=2)
+    finally:
+        assert srv.close() == 0
+    assert r["errors"] == 0 and r["mismatches"] == 0
+    assert (r["latency_us"] > 0).all()
+    assert r["wall_s"] >= t[-1] * 0.99
+
+
+def test_load_generator_refuses_bad_arguments():
+    lg = _lib.load_loadgen()
+    res = _lib.me_load_result()
+    assert lg.me_load_run(None, None, 0, None, 1, 1, None, None, ctypes.byref(res)) == \
+        _lib.C["ME_ERR_ARG"]
