@@ -449,6 +449,63 @@ def unpadded_leg(lib_mod, stream, peak):
             "exact": exact, "exact_images_checked": n}
 
 
+def outputs_leg(lib_mod, stream, peak, side=32768, rotate=3):
+    """The other outputs of one fused read on the 1-Gpixel image: the four
+    fundamental edges (1 word read, 4 written per word), the drawn polarity
+    and the end-point map (1 read, 1 written), rotating `rotate` input and
+    output sets past L2.  Each is checked against me_edges on the device:
+    the OR of the four fundamentals equals it, the drawn form is its
+    complement on the image's pixels, and end points are edge points."""
+    import torch
+    from paper_1401_5245_gb300 import synth
+    w = h = side
+    stride = w // 32
+    words = synth.bernoulli_half_packed(w, h, seed=5)
+    dev = torch.device("cuda")
+    xs = [torch.from_numpy(words.view(np.int32)).to(dev) for _ in range(rotate)]
+    outs = [[torch.empty_like(xs[0]) for _ in range(4)] for _ in range(rotate)]
+    L = lib_mod.load()
+    s = stream.cuda_stream
+    k = [0]
+    calls = {
+        "fundamental": (lambda x, o: L.me_fundamental_edges(x.data_ptr(), w, h, stride,
+                                                            o[0].data_ptr(), o[1].data_ptr(),
+                                                            o[2].data_ptr(), o[3].data_ptr(),
+                                                            0, s), 5),
+        "display": (lambda x, o: L.me_edges_display(x.data_ptr(), w, h, stride,
+                                                    o[0].data_ptr(), 0, s), 2),
+        "end_points": (lambda x, o: L.me_end_points(x.data_ptr(), w, h, stride,
+                                                    o[0].data_ptr(), 0, s), 2),
+    }
+    edge = torch.empty_like(xs[0])
+    lib_mod.check(L.me_edges(xs[0].data_ptr(), w, h, stride, edge.data_ptr(), 0, s))
+    res = {}
+    for name, (fn, words_moved) in calls.items():
+        def one():
+            i = k[0] % rotate
+            k[0] += 1
+            rc = fn(xs[i], outs[i])
+            if rc != 0:
+                raise lib_mod.MeError(rc, name)
+        lib_mod.check(fn(xs[0], outs[0]), name)
+        torch.cuda.synchronize()
+        o = outs[0]
+        if name == "fundamental":
+            ok = torch.equal(o[0] | o[1] | o[2] | o[3], edge)
+        elif name == "display":
+            ok = torch.equal(o[0], ~edge)            # w % 32 == 0: no padding bits
+        else:
+            ok = torch.equal(o[0] & ~edge, torch.zeros_like(edge))
+        one()
+        t = time_events(one, 30, stream)
+        nbytes = words_moved * h * stride * 4
+        res[name] = {"gpixel_s": round(w * h / t / 1e9, 1), "gb_s": round(nbytes / t / 1e9, 1),
+                     "frac_of_peak": round(nbytes / t / 1e9 / peak, 4), "us": round(t * 1e6, 2),
+                     "bytes_per_launch": nbytes, "consistent_with_me_edges": bool(ok)}
+    del xs, outs, edge
+    return res
+
+
 def serve_leg(lib_mod, n_requests=100000, loads=(0.25, 0.5, 0.8, 0.95), seed=0):
     """Serving: requests drawn from the 48x48 / 1024x1024 / 2480x3508 mix
     (70/25/5 %), an 8 GiB device budget, driven from C threads by the
@@ -853,6 +910,7 @@ def run_ours(args, rank, world, local_rank):
         del xs, ys
 
     if not args.quick:
+        extra["outputs_32768"] = outputs_leg(_lib, stream, peak)
         extra["threshold_8192"] = threshold_leg(_lib, stream, peak)
         extra["threshold_16384"] = threshold_leg(_lib, stream, peak, 16384)
         extra["threshold_otsu_16384"] = otsu_leg(_lib, stream, peak)

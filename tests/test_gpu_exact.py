@@ -272,6 +272,57 @@ def test_end_points_line():
     assert np.flatnonzero(got[2]).tolist() == [3, 59] and got.sum() == 2
 
 
+# --------------------------------------------- other outputs at full size
+def _big_images():
+    """4096 x 4096: Bernoulli(0.5) and 200 random thick polylines."""
+    return {"bernoulli": rand_img(40, 4096, 4096, 0.5),
+            "strokes": S.strokes(4096, 4096, 200, 41)}
+
+
+OUTPUT_KINDS = {
+    "fundamental": (fund_call, 4, lambda img, b: O.fundamental(img, b)),
+    "display": (lambda *a: _lib.load().me_edges_display(*a), 1,
+                lambda img, b: (1 - O.edges(img, b),)),
+    "end_points": (lambda *a: _lib.load().me_end_points(*a), 1,
+                   lambda img, b: (O.end_points(img, b),)),
+}
+
+
+@pytest.fixture(scope="module")
+def big_images():
+    return _big_images()
+
+
+@pytest.mark.parametrize("kind", sorted(OUTPUT_KINDS))
+@pytest.mark.parametrize("name", ["bernoulli", "strokes"])
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_other_outputs_4096(big_images, kind, name, boundary):
+    """Tall multi-tile columns on the 128-bit path: every output of every
+    pixel against the oracle."""
+    fn, n_out, oracle_fn = OUTPUT_KINDS[kind]
+    img = big_images[name]
+    got = run_single(fn, img, stride=128, boundary=boundary, n_out=n_out)
+    got = got if n_out > 1 else [got]
+    for k, (g_, w_) in enumerate(zip(got, oracle_fn(img, boundary))):
+        assert np.array_equal(g_, w_), (kind, name, boundary, k)
+
+
+@pytest.mark.parametrize("kind", sorted(OUTPUT_KINDS))
+@pytest.mark.parametrize("w,h,extra", [(4097, 1500, 3), (32768, 160, 0)])
+def test_other_outputs_wide_rows(kind, w, h, extra):
+    """Rows wider than 32 vector columns: overlapping warps over column
+    blocks (4097: one block and a ragged one; 32768: 35 blocks), compared
+    in full against the oracle, both boundaries."""
+    fn, n_out, oracle_fn = OUTPUT_KINDS[kind]
+    img = S.strokes(w, h, 60, w + h) if w < 32768 else rand_img(42, h, w, 0.5)
+    stride = S.round_up(S.words_per_row(w), 4) + extra
+    for boundary in (0, 1):
+        got = run_single(fn, img, stride=stride, boundary=boundary, n_out=n_out)
+        got = got if n_out > 1 else [got]
+        for k, (g_, w_) in enumerate(zip(got, oracle_fn(img, boundary))):
+            assert np.array_equal(g_, w_), (kind, w, h, boundary, k)
+
+
 # ------------------------------------------------------------- error paths
 def test_host_pointer_is_rejected():
     words = np.zeros((8, 1), dtype=np.uint32)

@@ -84,15 +84,20 @@ def test_two_columns_per_thread():
     assert np.array_equal(run_inplace(img, 0, S.batch_stride(w)), O.edges(img, 0))
 
 
-def test_matches_out_of_place_on_a_large_image():
+def test_large_image_against_the_oracle():
+    """16384 x 8192 (512 MiB of bands and seams on the band route): the
+    result over the image equals the oracle's edge map and me_edges."""
     import torch
     w, h = 16384, 8192
     words = S.bernoulli_half_packed(w, h, seed=4)
+    want = O.edges(S.unpack(words, w), 0)
     x = torch.from_numpy(words.view(np.int32)).cuda()
     ref = torch.empty_like(x)
     assert _lib.me_edges(x, w, h, 512, ref, 0) == 0
     assert _lib.me_edges_inplace(x, w, h, 512, 0) == 0
     sync()
+    got = x.cpu().numpy().view(np.uint32)
+    assert np.array_equal(S.unpack(got, w), want)
     assert torch.equal(x, ref)
 
 
