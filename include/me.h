@@ -447,6 +447,35 @@ int me_serve_poll(me_server *srv, uint64_t ticket, uint32_t *host_edge,
                   int64_t timeout_us, me_timing *t);
 
 /*
+ * Zero-copy submit.  Reserves room for one image (h rows of stride_words
+ * words) in the server's pinned staging and points *host_img at it; the
+ * caller writes the image there and then calls me_serve_commit.  The
+ * request joins the queue at once, in arrival order, but neither it nor
+ * the requests behind it are admitted before it is committed, so commit
+ * promptly.  ME_PENDING (nothing reserved) when staging has no room now:
+ * retry, or use me_serve_submit, which waits in heap memory.  Otherwise
+ * errors as me_serve_submit.  A reserved request may be cancelled.
+ */
+int me_serve_reserve(me_server *srv, int32_t w, int32_t h, int32_t stride_words,
+                     int32_t boundary, uint64_t *ticket, uint32_t **host_img);
+
+/* The image of a reserved ticket is written: the request may be admitted.
+ * ME_ERR_ARG for a ticket that is not reserved or is committed already. */
+int me_serve_commit(me_server *srv, uint64_t ticket);
+
+/*
+ * Zero-copy collect: waits as me_serve_poll, then points *host_edge at the
+ * edge map in the server's staging instead of copying it out.  The edge
+ * map stays there, and the ticket known, until me_serve_release(ticket).
+ */
+int me_serve_poll_view(me_server *srv, uint64_t ticket, int64_t timeout_us,
+                       const uint32_t **host_edge, me_timing *t);
+
+/* Give back the staging of a finished ticket and forget it (after
+ * me_serve_poll_view).  ME_ERR_ARG while the request is unfinished. */
+int me_serve_release(me_server *srv, uint64_t ticket);
+
+/*
  * Forget a ticket.  A request still queued is dropped at once; one already
  * on the GPU finishes there and its memory is reclaimed when its batch
  * retires; a finished one is freed.  ME_ERR_TICKET for an unknown ticket;

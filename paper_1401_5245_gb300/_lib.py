@@ -112,6 +112,12 @@ PROTOTYPES = {
                                        ctypes.POINTER(c_u64)]),
     "me_serve_poll": (ctypes.c_int, [c_vp, c_u64, c_vp, c_i64, ctypes.POINTER(me_timing)]),
     "me_serve_cancel": (ctypes.c_int, [c_vp, c_u64]),
+    "me_serve_reserve": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(c_u64),
+                                        ctypes.POINTER(c_vp)]),
+    "me_serve_commit": (ctypes.c_int, [c_vp, c_u64]),
+    "me_serve_poll_view": (ctypes.c_int, [c_vp, c_u64, c_i64, ctypes.POINTER(c_vp),
+                                          ctypes.POINTER(me_timing)]),
+    "me_serve_release": (ctypes.c_int, [c_vp, c_u64]),
     "me_serve_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                                       ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     "me_serve_copies": (ctypes.c_int, [c_vp, ctypes.POINTER(c_i64)]),
@@ -342,6 +348,38 @@ class Server:
     def cancel(self, ticket) -> int:
         return load().me_serve_cancel(self._h, ticket)
 
+    def reserve(self, w, h, stride_words, boundary=0):
+        """Zero-copy submit, step 1: (status, ticket, numpy view of the
+        staging to write the h x stride_words image into)."""
+        import numpy as np
+        t, p = c_u64(), c_vp()
+        rc = load().me_serve_reserve(self._h, w, h, stride_words, boundary, ctypes.byref(t),
+                                     ctypes.byref(p))
+        if rc != 0:
+            return rc, 0, None
+        buf = (ctypes.c_uint32 * (h * stride_words)).from_address(p.value)
+        return rc, t.value, np.ctypeslib.as_array(buf).reshape(h, stride_words)
+
+    def commit(self, ticket) -> int:
+        return load().me_serve_commit(self._h, ticket)
+
+    def poll_view(self, ticket, h, stride_words, timeout_us=-1):
+        """Zero-copy collect: (status, timing, read-only numpy view of the
+        edge map in the server's staging, valid until release)."""
+        import numpy as np
+        tm, p = me_timing(), c_vp()
+        rc = load().me_serve_poll_view(self._h, ticket, timeout_us, ctypes.byref(p),
+                                       ctypes.byref(tm))
+        if rc != 0:
+            return rc, tm, None
+        buf = (ctypes.c_uint32 * (h * stride_words)).from_address(p.value)
+        v = np.ctypeslib.as_array(buf).reshape(h, stride_words)
+        v.flags.writeable = False
+        return rc, tm, v
+
+    def release(self, ticket) -> int:
+        return load().me_serve_release(self._h, ticket)
+
     def stats(self):
         v = [c_i64() for _ in range(5)]
         check(load().me_serve_stats(self._h, *[ctypes.byref(x) for x in v[:4]]),
@@ -397,17 +435,19 @@ def load_loadgen() -> ctypes.CDLL:
             dp = ctypes.POINTER(ctypes.c_double)
             lg.me_load_run.restype = ctypes.c_int
             lg.me_load_run.argtypes = [c_vp, ctypes.POINTER(me_load_item), c_i64, dp, c_i32,
-                                       c_i32, dp, dp, ctypes.POINTER(me_load_result)]
+                                       c_i32, c_i32, dp, dp, ctypes.POINTER(me_load_result)]
             _loadgen = lg
     return _loadgen
 
 
-def load_run(server: "Server", reqs, expect=None, arrival_s=None, clients=4, window=32):
+def load_run(server: "Server", reqs, expect=None, arrival_s=None, clients=4, window=32,
+             zero_copy=False):
     """Drive `server` with the requests `reqs` (objects with .words, .w, .h,
     .stride_words, .boundary) from C threads (me_load_run).  expect: None or
     one edge-map array per request to compare with.  arrival_s: None for a
     closed loop of `window` outstanding requests per client, else the
-    arrival times in seconds (open loop).  Returns wall_s, mismatches,
+    arrival times in seconds (open loop).  zero_copy: the clients write into
+    reserved staging and read results in place.  Returns wall_s, mismatches,
     errors, first_error and the per-request latency_us / server_us arrays."""
     import numpy as np
     n = len(reqs)
@@ -426,7 +466,8 @@ def load_run(server: "Server", reqs, expect=None, arrival_s=None, clients=4, win
     res = me_load_result()
     check(load_loadgen().me_load_run(
         server.handle, items, n, arr.ctypes.data_as(dp) if arr is not None else None,
-        clients, window, lat.ctypes.data_as(dp), srv_us.ctypes.data_as(dp),
+        clients, window, 1 if zero_copy else 0, lat.ctypes.data_as(dp),
+        srv_us.ctypes.data_as(dp),
         ctypes.byref(res)), "me_load_run")
     return {"wall_s": res.wall_s, "mismatches": res.mismatches, "errors": res.errors,
             "first_error": res.first_error, "latency_us": lat, "server_us": srv_us}

@@ -11,7 +11,10 @@
 // from the submit call (closed loop) to the return of the poll that
 // delivered the result, so a client or server that falls behind its
 // schedule shows in it.  Every result can be compared with the edge map it
-// must equal.
+// must equal.  With zero_copy the clients use the server's zero-copy calls:
+// each writes its image straight into the staging it reserved and reads the
+// edge map where the server left it (an XOR over its words stands for the
+// client consuming it), instead of one copy in and one copy out.
 //
 // Not part of libme's C ABI; bench.py and the serving tests load it.
 #include <algorithm>
@@ -63,11 +66,14 @@ typedef struct me_load_result {
     int64_t mismatches;        // results that differed from expect
     int64_t errors;            // failed submits or polls
     int32_t first_error;       // status of the first failure (0: none)
-    int32_t pad;
+    int32_t pad;               // zero-copy clients: bits of the XOR of what they read
 } me_load_result;
 
 /*
  * Run n requests through srv.  Request i goes to client i % clients.
+ * zero_copy: submit by me_serve_reserve / me_serve_commit and collect by
+ * me_serve_poll_view / me_serve_release (else me_serve_submit and
+ * me_serve_poll).
  * arrival_us: NULL for a closed loop (each client keeps up to `window`
  * requests outstanding), else the arrival time of each request in
  * microseconds from the start (open loop; window is ignored).
@@ -78,12 +84,14 @@ typedef struct me_load_result {
  */
 int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                 const double *arrival_us, int32_t clients, int32_t window,
-                double *latency_us, double *server_us, me_load_result *res) {
+                int32_t zero_copy, double *latency_us, double *server_us,
+                me_load_result *res) {
     if (srv == nullptr || items == nullptr || n <= 0 || clients < 1 || res == nullptr ||
         (arrival_us == nullptr && window < 1))
         return ME_ERR_ARG;
     std::memset(res, 0, sizeof(*res));
     std::atomic<int64_t> mismatches{0}, errors{0};
+    std::atomic<uint64_t> checksum{0};
     std::atomic<int32_t> first_error{0};
     auto fail = [&](int rc) {
         errors.fetch_add(1);
@@ -126,8 +134,27 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                     const me_load_item &it = items[next];
                     const auto from = open ? arrival(next) : Clock::now();
                     uint64_t tk = 0;
-                    const int rc = me_serve_submit(srv, it.img, it.w, it.h, it.stride_words,
-                                                   it.boundary, &tk);
+                    int rc;
+                    if (zero_copy) {
+                        uint32_t *dst = nullptr;
+                        rc = me_serve_reserve(srv, it.w, it.h, it.stride_words, it.boundary,
+                                              &tk, &dst);
+                        if (rc == ME_PENDING && !out.empty()) {
+                            // no staging now: collect the oldest result first
+                            goto collect;
+                        }
+                        if (rc == ME_PENDING) {
+                            std::this_thread::yield();
+                            continue;
+                        }
+                        if (rc == ME_OK) {
+                            std::memcpy(dst, it.img, (size_t)it.h * (size_t)it.stride_words * 4);
+                            rc = me_serve_commit(srv, tk);
+                        }
+                    } else {
+                        rc = me_serve_submit(srv, it.img, it.w, it.h, it.stride_words,
+                                             it.boundary, &tk);
+                    }
                     if (rc == ME_OK) out.push_back({next, tk, from}); else fail(rc);
                     next += clients;
                     continue;
@@ -136,26 +163,40 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                     wait_until(arrival(next));
                     continue;
                 }
+            collect : {
                 // the oldest result, waiting no longer than the next arrival
                 int64_t timeout = -1;
                 if (open && next < n)
-                    timeout = (int64_t)std::max(0.0, us_between(now, arrival(next)));
+                    timeout = (int64_t)std::max(0.0, us_between(Clock::now(), arrival(next)));
                 me_timing tm{};
                 const Out o = out.front();
-                const int rc = me_serve_poll(srv, o.ticket, scratch.data(), timeout, &tm);
+                const uint32_t *view = nullptr;
+                const int rc = zero_copy
+                                   ? me_serve_poll_view(srv, o.ticket, timeout, &view, &tm)
+                                   : me_serve_poll(srv, o.ticket, scratch.data(), timeout, &tm);
                 if (rc == ME_PENDING || rc == ME_TIMEOUT) continue;
                 out.pop_front();
-                last = Clock::now();
                 if (rc != ME_OK) {
                     fail(rc);
+                    if (zero_copy) me_serve_release(srv, o.ticket);
+                    last = Clock::now();
                     continue;
                 }
+                const me_load_item &it = items[o.i];
+                const size_t bytes = (size_t)it.h * (size_t)it.stride_words * 4;
+                const uint32_t *got = zero_copy ? view : scratch.data();
+                if (it.expect) {
+                    if (std::memcmp(got, it.expect, bytes) != 0) mismatches.fetch_add(1);
+                } else if (zero_copy) {
+                    uint64_t x = 0;
+                    for (size_t k = 0; k < bytes / 4; ++k) x ^= got[k];
+                    checksum.fetch_xor(x, std::memory_order_relaxed);
+                }
+                if (zero_copy) me_serve_release(srv, o.ticket);
+                last = Clock::now();
                 if (latency_us) latency_us[o.i] = us_between(o.from, last);
                 if (server_us) server_us[o.i] = tm.total_us;
-                const me_load_item &it = items[o.i];
-                if (it.expect && std::memcmp(scratch.data(), it.expect,
-                                             (size_t)it.h * (size_t)it.stride_words * 4) != 0)
-                    mismatches.fetch_add(1);
+            }
             }
             t_last[c] = last;
         });
@@ -170,6 +211,7 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
     res->mismatches = mismatches.load();
     res->errors = errors.load();
     res->first_error = first_error.load();
+    res->pad = (int32_t)(checksum.load() & 0x7fffffff);
     return ME_OK;
 }
 

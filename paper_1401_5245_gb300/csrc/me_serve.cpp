@@ -64,6 +64,9 @@ double us_since(Clock::time_point a, Clock::time_point b) {
 
 constexpr size_t kAlign = 256;
 constexpr int kShards = 16;
+// A poller watches its request this long before it sleeps: most requests
+// finish meanwhile, and the completion thread then makes no wake-up call.
+constexpr int kSpinUs = 30;
 
 enum State { QUEUED, ADMITTED, DONE, FAILED };
 
@@ -77,8 +80,11 @@ struct Req {
     size_t pin_off = 0;                // staging: input at in + off, output at out + off
     std::unique_ptr<uint32_t[]> heap;  // input while staging was full
     size_t dev_off = 0;                // device: input at in + off, output at out + off
-    State state = QUEUED;              // QUEUED->ADMITTED under qmu, then under the shard
+    // QUEUED -> ADMITTED under qmu, then DONE or FAILED under the shard;
+    // atomic so that a poller may watch it without the lock
+    std::atomic<State> state{QUEUED};
     bool cancelled = false;            // under qmu and the shard
+    bool open = false;                 // reserved, not yet committed (qmu and the shard)
     // the condition the poller waiting for this request sleeps on (only that
     // poller is woken when the request's batch retires); under the shard
     std::condition_variable *waiter = nullptr;
@@ -110,6 +116,36 @@ void for_each_run(const std::vector<Req *> &reqs, F &&f) {
         f(reqs[i], reqs[j]);
         i = j + 1;
     }
+}
+
+bool finished(const Req *r) {
+    const State st = r->state.load();
+    return st == DONE || st == FAILED;
+}
+
+// Wait until r has finished, at most timeout_us (negative: no limit).  sl
+// holds r's shard lock on entry and on return.  ME_OK, ME_PENDING (timeout
+// 0), ME_TIMEOUT, or ME_ERR_ARG when another thread already waits for r.
+int wait_finished(std::unique_lock<std::mutex> &sl, Req *r, int64_t timeout_us) {
+    if (finished(r)) return ME_OK;
+    if (timeout_us == 0) return ME_PENDING;
+    if (r->waiter != nullptr) return ME_ERR_ARG;
+    std::condition_variable cv;
+    r->waiter = &cv;                   // from here on cancel refuses the ticket
+    const auto t0 = Clock::now();
+    const int64_t spin = timeout_us < 0 ? kSpinUs : std::min<int64_t>(kSpinUs, timeout_us);
+    sl.unlock();
+    const auto spin_end = t0 + std::chrono::microseconds(spin);
+    while (!finished(r) && Clock::now() < spin_end) std::this_thread::yield();
+    sl.lock();
+    bool ok = true;
+    if (timeout_us < 0)
+        cv.wait(sl, [r] { return finished(r); });
+    else
+        ok = cv.wait_until(sl, t0 + std::chrono::microseconds(timeout_us),
+                           [r] { return finished(r); });
+    r->waiter = nullptr;
+    return ok ? ME_OK : ME_TIMEOUT;
 }
 
 }  // namespace
@@ -593,19 +629,9 @@ int me_serve_poll(me_server *s, uint64_t ticket, uint32_t *host_edge, int64_t ti
     auto it = sh.map.find(ticket);
     if (it == sh.map.end()) return ME_ERR_TICKET;
     Req *r = it->second;
-    auto ready = [r] { return r->state == DONE || r->state == FAILED; };
-    if (!ready()) {
-        if (timeout_us == 0) return ME_PENDING;
-        if (r->waiter != nullptr) return ME_ERR_ARG;      // another thread polls it
-        std::condition_variable cv;
-        r->waiter = &cv;
-        bool ok = true;
-        if (timeout_us < 0)
-            cv.wait(sl, ready);
-        else
-            ok = cv.wait_for(sl, std::chrono::microseconds(timeout_us), ready);
-        r->waiter = nullptr;
-        if (!ok) return ME_TIMEOUT;
+    if (!finished(r)) {
+        const int rc = wait_finished(sl, r, timeout_us);
+        if (rc != ME_OK) return rc;
         it = sh.map.find(ticket);           // the map may have rehashed meanwhile
     }
     sh.map.erase(it);
@@ -638,7 +664,9 @@ int me_serve_cancel(me_server *s, uint64_t ticket) {
     sh.map.erase(it);
     if (r->state == QUEUED) {
         s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
-        if (!r->copied.load()) {
+        if (r->open) {
+            s->free_req(r);                 // reserved, never committed
+        } else if (!r->copied.load()) {
             r->cancelled = true;            // the engine is copying it in; it frees it
         } else {
             if (!r->pinned) --s->heap_waiting;
@@ -650,6 +678,100 @@ int me_serve_cancel(me_server *s, uint64_t ticket) {
         s->free_req(r);
     }
     s->wake_engine_locked();
+    return ME_OK;
+}
+
+int me_serve_reserve(me_server *s, int32_t w, int32_t h, int32_t stride_words,
+                     int32_t boundary, uint64_t *ticket, uint32_t **host_img) {
+    if (s == nullptr || ticket == nullptr || host_img == nullptr) return ME_ERR_ARG;
+    if (w <= 0 || h <= 0 || stride_words < (int32_t)(((int64_t)w + 31) / 32) ||
+        (boundary != ME_BOUNDARY_WHITE && boundary != ME_BOUNDARY_BLACK))
+        return ME_ERR_ARG;
+    std::unique_ptr<Req> r(new (std::nothrow) Req());
+    if (!r) return ME_ERR_NOMEM;
+    r->w = w;
+    r->h = h;
+    r->stride = stride_words;
+    r->boundary = boundary;
+    r->bytes = (size_t)h * (size_t)stride_words * 4;
+    r->span = (r->bytes + kAlign - 1) / kAlign * kAlign;
+    r->t_submit = Clock::now();
+    r->open = true;
+    Req *p = r.get();
+    {
+        std::lock_guard<std::mutex> lk(s->qmu);
+        if (s->closing) return ME_ERR_CLOSED;
+        if (p->span > s->dev_half || p->span > s->pin_half) return ME_ERR_BUDGET;
+        s->drain_freed();
+        if (!s->pin_alloc.alloc_next(p->span, &p->pin_off)) return ME_PENDING;
+        p->pinned = true;
+        p->ticket = s->next_ticket++;
+        s->queue.push_back(p);
+        if (s->queue.size() == 1 && s->engine_waiting.load()) s->waits_for.store(p);
+    }
+    {
+        Shard &sh = s->shard(p->ticket);
+        std::lock_guard<std::mutex> sl(sh.mu);
+        sh.map[p->ticket] = p;
+    }
+    r.release();
+    ++s->submitted;
+    *ticket = p->ticket;
+    *host_img = reinterpret_cast<uint32_t *>(s->pin_in(p));
+    return ME_OK;
+}
+
+int me_serve_commit(me_server *s, uint64_t ticket) {
+    if (s == nullptr) return ME_ERR_ARG;
+    Req *p = nullptr;
+    {
+        Shard &sh = s->shard(ticket);
+        std::lock_guard<std::mutex> sl(sh.mu);
+        auto it = sh.map.find(ticket);
+        if (it == sh.map.end()) return ME_ERR_TICKET;
+        p = it->second;
+        if (!p->open) return ME_ERR_ARG;      // not reserved, or committed already
+        p->open = false;
+    }
+    p->copied.store(true);
+    if (s->waits_for.load() == p) s->wake_engine();
+    return ME_OK;
+}
+
+int me_serve_poll_view(me_server *s, uint64_t ticket, int64_t timeout_us,
+                       const uint32_t **host_edge, me_timing *t) {
+    if (s == nullptr || host_edge == nullptr) return ME_ERR_ARG;
+    Shard &sh = s->shard(ticket);
+    std::unique_lock<std::mutex> sl(sh.mu);
+    auto it = sh.map.find(ticket);
+    if (it == sh.map.end()) return ME_ERR_TICKET;
+    Req *r = it->second;
+    const int rc = wait_finished(sl, r, timeout_us);
+    if (rc != ME_OK) return rc;
+    if (r->state == FAILED) return ME_ERR_CUDA;
+    *host_edge = reinterpret_cast<const uint32_t *>(s->pin_out(r));
+    if (t) {
+        t->queue_us = us_since(r->t_submit, r->t_admit);
+        t->device_us = us_since(r->t_admit, r->t_done);
+        t->total_us = us_since(r->t_submit, r->t_done);
+    }
+    return ME_OK;
+}
+
+int me_serve_release(me_server *s, uint64_t ticket) {
+    if (s == nullptr) return ME_ERR_ARG;
+    Req *r = nullptr;
+    {
+        Shard &sh = s->shard(ticket);
+        std::lock_guard<std::mutex> sl(sh.mu);
+        auto it = sh.map.find(ticket);
+        if (it == sh.map.end()) return ME_ERR_TICKET;
+        r = it->second;
+        if (r->state != DONE && r->state != FAILED) return ME_ERR_ARG;
+        sh.map.erase(it);
+    }
+    s->push_freed(r);
+    if (s->heap_waiting.load() > 0) s->wake_engine();
     return ME_OK;
 }
 
@@ -722,7 +844,7 @@ int me_serve_close(me_server *s, int64_t drain_timeout_us) {
                 std::lock_guard<std::mutex> sl(sh.mu);
                 sh.map.erase(r->ticket);
             }
-            if (!r->copied.load()) r->cancelled = true;
+            if (!r->copied.load() && !r->open) r->cancelled = true;
             else s->free_req(r);
         }
         s->queue.clear();

@@ -244,5 +244,84 @@ def test_load_generator_open_loop_and_black_boundary(pool):
 def test_load_generator_refuses_bad_arguments():
     lg = _lib.load_loadgen()
     res = _lib.me_load_result()
-    assert lg.me_load_run(None, None, 0, None, 1, 1, None, None, ctypes.byref(res)) == \
+    assert lg.me_load_run(None, None, 0, None, 1, 1, 0, None, None, ctypes.byref(res)) == \
         _lib.C["ME_ERR_ARG"]
+
+
+# ------------------------------------------------------------- zero copy
+def test_zero_copy_reserve_commit_view_release(pool):
+    """Images written straight into reserved staging and edge maps read
+    where the server leaves them: every one is the oracle's; a reserved
+    request can be cancelled; release refuses unfinished tickets; commit
+    refuses tickets that are not open."""
+    srv = _lib.Server(hbm_budget_bytes=256 << 20, staging_bytes=256 << 20, max_inflight=2,
+                      max_batch=8, tick_us=0)
+    try:
+        tickets = []
+        for im in pool:
+            rc, t, dst = srv.reserve(im.w, im.h, im.stride_words, im.boundary)
+            assert rc == 0
+            dst[...] = im.words
+            tickets.append((im, t))
+        # one more, reserved and cancelled before it is committed
+        rc, tx, _ = srv.reserve(40, 3, 2)
+        assert rc == 0
+        assert srv.release(tickets[0][1]) == _lib.C["ME_ERR_ARG"]     # not finished
+        assert srv.cancel(tx) == 0
+        for im, t in tickets:
+            assert srv.commit(t) == 0
+        assert srv.commit(tickets[0][1]) == _lib.C["ME_ERR_ARG"]      # committed already
+        for im, t in tickets:
+            rc, tm, view = srv.poll_view(t, im.h, im.stride_words)
+            assert rc == 0 and tm.total_us >= tm.device_us >= 0
+            assert np.array_equal(S.unpack(view, im.w),
+                                  O.edges(S.unpack(im.words, im.w), im.boundary)), (im.w, im.h)
+            assert srv.release(t) == 0
+            assert srv.release(t) == _lib.C["ME_ERR_TICKET"]
+        st = srv.stats()
+        assert st["completed"] == len(pool)
+    finally:
+        assert srv.close() == 0
+
+
+def test_zero_copy_staging_full_is_pending(pool):
+    """Staging for one request: a second reservation reports ME_PENDING
+    (nothing reserved) until the first is released."""
+    a = max(pool, key=lambda im: im.packed_bytes)
+    span = (a.packed_bytes + 255) // 256 * 256
+    srv = _lib.Server(hbm_budget_bytes=64 << 20, staging_bytes=2 * span, max_inflight=1,
+                      max_batch=1, tick_us=0)
+    try:
+        rc, t, dst = srv.reserve(a.w, a.h, a.stride_words)
+        assert rc == 0
+        dst[...] = a.words
+        assert srv.reserve(a.w, a.h, a.stride_words)[0] == _lib.C["ME_PENDING"]
+        assert srv.commit(t) == 0
+        rc, _, view = srv.poll_view(t, a.h, a.stride_words)
+        assert rc == 0
+        assert srv.reserve(a.w, a.h, a.stride_words)[0] == _lib.C["ME_PENDING"]
+        assert srv.release(t) == 0
+        rc, t2, dst2 = srv.reserve(a.w, a.h, a.stride_words)
+        assert rc == 0
+        assert srv.cancel(t2) == 0
+    finally:
+        assert srv.close() == 0
+
+
+def test_load_generator_zero_copy_every_result_is_the_oracles(pool):
+    want = {id(im): oracle_words(im) for im in pool}
+    g = np.random.default_rng(8)
+    reqs = [pool[int(i)] for i in g.integers(0, len(pool), 3000)]
+    srv = _lib.Server(hbm_budget_bytes=1 << 30, staging_bytes=256 << 20, max_inflight=2,
+                      max_batch=512, tick_us=0)
+    try:
+        r = _lib.load_run(srv, reqs, expect=[want[id(im)] for im in reqs], clients=4,
+                          window=32, zero_copy=True)
+        r2 = _lib.load_run(srv, reqs, arrival_s=np.cumsum(g.exponential(1e-5, len(reqs))),
+                           clients=3, zero_copy=True)
+        st = srv.stats()
+    finally:
+        assert srv.close() == 0
+    assert r["errors"] == 0 and r["mismatches"] == 0
+    assert r2["errors"] == 0
+    assert st["completed"] == 2 * len(reqs)
