@@ -114,9 +114,11 @@ int me_edges(const uint32_t *img, int32_t w, int32_t h, int32_t stride_words,
  *                                          (Section 4 edges ORed, Section 5)
  * It moves about 17 bits of HBM traffic per pixel instead of 2 and is kept
  * as the baseline form.  Arguments as me_edges.  The mask image M is
- * scratch the library takes from CUDA's stream-ordered allocator on
- * `stream` and returns after pass 5 (h * stride_words * 4 bytes); failure
- * to get it returns ME_ERR_CUDA with nothing enqueued.
+ * scratch (h * stride_words * 4 bytes) the library takes on `stream` from a
+ * stream-ordered memory pool it owns on each device and returns after pass
+ * 5; the pool keeps up to 512 MiB reserved between calls, until
+ * me_shutdown().  Failure to get it returns ME_ERR_CUDA with nothing
+ * enqueued.
  */
 int me_edges_staged(const uint32_t *img, int32_t w, int32_t h,
                     int32_t stride_words, uint32_t *edge, int32_t boundary,
@@ -193,8 +195,9 @@ int me_end_points(const uint32_t *img, int32_t w, int32_t h,
  * is overwritten only after every read of its original bits, and the two
  * rows on either side of every band seam are first copied to scratch
  * (2 * (bands - 1) * stride_words * 4 bytes, bands = about 4 per SM, at
- * least 32 rows each).  Scratch comes from CUDA's stream-ordered allocator
- * on `stream` and is returned when the call's work is done.
+ * least 32 rows each).  Scratch comes from the library's stream-ordered
+ * pool on `stream` (as for me_edges_staged) and is returned when the call's
+ * work is done.
  *
  * img           device pointer, 4-byte aligned; 128-bit accesses when it
  *               is 16-byte aligned and stride_words % 4 == 0.
@@ -246,7 +249,8 @@ int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int32_t pitch_
  * grey, w, h, pitch_bytes, edge, stride_words, binary, boundary, stream
  *               as me_threshold_edges.
  * threshold_out NULL, or a 4-byte aligned device int32 that receives t.
- * Scratch of about 2 KB comes from the stream-ordered allocator; failure to
+ * Scratch of about 2 KB comes from the library's stream-ordered pool (as
+ * for me_edges_staged); failure to
  * get it returns ME_ERR_CUDA with nothing enqueued.  threshold_out must not
  * overlap grey, edge or binary (ME_ERR_ALIAS).
  */
@@ -517,8 +521,9 @@ int me_serve_close(me_server *srv, int64_t drain_timeout_us);
  */
 int me_device_faults(int32_t clear, uint32_t *flags);
 
-/* Free the batch rings, graphs and plans' shared state on every device,
- * and forget the device addresses me_edges_staged_static has looked up. */
+/* Free the batch rings, graphs and plans' shared state and the scratch
+ * pools on every device (synchronising each), and forget the device
+ * addresses me_edges_staged_static has looked up. */
 int me_shutdown(void);
 
 #ifdef __cplusplus

@@ -230,13 +230,13 @@ int me_edges_staged(const uint32_t *img, int32_t w, int32_t h,
     const cudaStream_t s = (cudaStream_t)stream;
     const Geo g = make_geo(img, w, h, stride_words, boundary, 1);
     uint32_t *mask = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&mask, (size_t)h * stride_words * 4, s);
+    cudaError_t e = scratch_alloc((void **)&mask, (size_t)h * stride_words * 4, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return record_cuda(e);
     }
     e = launch_staged(g, mask, edge, s);
-    cudaError_t f = cudaFreeAsync(mask, s);
+    cudaError_t f = scratch_free(mask, s);
     if (e == cudaSuccess) e = f;
     return e == cudaSuccess ? ME_OK : record_cuda(e);
 }

@@ -369,6 +369,7 @@ int me_batch_plan_destroy(me_batch_plan *plan) {
 int me_shutdown(void) {
     host_pipes_shutdown();
     static_forget_all();
+    scratch_shutdown();
     return batch_shutdown_all();
 }
 

@@ -129,6 +129,10 @@ k_inplace(IpGeo g) {
         return make_uint4(fix(r.x, kp[0]), fix(r.y, kp[1]), fix(r.z, kp[2]), fix(r.w, kp[3]));
     };
 
+    // launched while the seam kernel may still run (programmatic dependent
+    // launch): wait for it to finish before the first read of the image or
+    // the seam rows
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int r = y0 - 1; r <= y0 + Q - G - 2; ++r) issue(r);
 
     const int lane = threadIdx.x & 31;
@@ -198,6 +202,9 @@ k_inplace(IpGeo g) {
 template <bool V16>
 __global__ void __launch_bounds__(256)
 k_seams(const uint32_t *img, uint32_t *seam, int32_t stride, int32_t band_rows) {
+    // the band kernel may be scheduled now; it waits for this grid to end
+    // before it reads anything
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const size_t words = 2 * (size_t)stride;
     const uint32_t *src = img + ((size_t)(blockIdx.x + 1) * band_rows - 1) * (size_t)stride;
     uint32_t *dst = seam + (size_t)blockIdx.x * words;
@@ -234,8 +241,21 @@ cudaError_t launch_inplace(const IpGeo &g, int threads, cudaStream_t s) {
             if (dev < 64) done[dev] = true;
         }
     }
-    k_inplace<C, V16, Q, G><<<g.nbands, threads, inplace_smem<C, Q>(threads), s>>>(g);
-    return cudaGetLastError();
+    // programmatic dependent launch: the band kernel's CTAs are placed and
+    // set up while the seam kernel before it finishes
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.nbands);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = inplace_smem<C, Q>(threads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_inplace<C, V16, Q, G>, g);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
 }
 
 }  // namespace
@@ -257,7 +277,7 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
     const size_t img_bytes = (size_t)h * (size_t)stride_words * 4;
     if (img_bytes <= copy_max()) {
         uint32_t *copy = nullptr;
-        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&copy), img_bytes, s);
+        cudaError_t e = scratch_alloc(reinterpret_cast<void **>(&copy), img_bytes, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return record_cuda(e);
@@ -267,7 +287,7 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
             rc = me_edges(copy, w, h, stride_words, img, boundary, stream);
             if (rc != ME_OK) e = cudaErrorLaunchFailure;
         }
-        const cudaError_t f = cudaFreeAsync(copy, s);
+        const cudaError_t f = scratch_free(copy, s);
         if (e != cudaSuccess || f != cudaSuccess) {
             cudaGetLastError();
             return rc != ME_OK ? rc : record_cuda(e != cudaSuccess ? e : f);
@@ -302,7 +322,7 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
     cudaError_t e = cudaSuccess;
     if (g.nbands > 1) {
         const size_t bytes = (size_t)2 * (g.nbands - 1) * (size_t)stride_words * 4;
-        if ((e = cudaMallocAsync(reinterpret_cast<void **>(&seam), bytes, s)) != cudaSuccess) {
+        if ((e = scratch_alloc(reinterpret_cast<void **>(&seam), bytes, s)) != cudaSuccess) {
             cudaGetLastError();
             return record_cuda(e);
         }
@@ -324,7 +344,7 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
                        : launch_inplace<2, false, 6, 2>(g, threads, s);
     }
     if (seam != nullptr) {
-        const cudaError_t f = cudaFreeAsync(seam, s);
+        const cudaError_t f = scratch_free(seam, s);
         if (e == cudaSuccess) e = f;
     }
     if (e != cudaSuccess) {

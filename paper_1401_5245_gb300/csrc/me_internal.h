@@ -310,6 +310,12 @@ class BatchRing {
 // Release the host-batch pipelines (streams, device slots) on every device.
 int host_pipes_shutdown();
 
+// Scratch from the library's stream-ordered pool on the current device
+// (kept reserved between calls up to a limit; me_shutdown destroys it).
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+cudaError_t scratch_free(void *p, cudaStream_t s);
+int scratch_shutdown();
+
 // Forget the device addresses me_edges_staged_static has cached.
 void static_forget_all();
 

@@ -454,7 +454,7 @@ extern "C" int me_threshold_edges_otsu(const uint8_t *grey, int32_t w, int32_t h
     // scratch: the histogram (256 counters) and, if the caller gave no
     // place for it, the threshold
     unsigned long long *hist = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&hist), 256 * 8 + 16, s);
+    cudaError_t e = scratch_alloc(reinterpret_cast<void **>(&hist), 256 * 8 + 16, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return record_cuda(e);
@@ -472,7 +472,7 @@ extern "C" int me_threshold_edges_otsu(const uint8_t *grey, int32_t w, int32_t h
         fn<<<grid, 32 * kThrWarps, 0, s>>>(g, ntasks, t_dev);
         e = cudaGetLastError();
     }
-    const cudaError_t f = cudaFreeAsync(hist, s);
+    const cudaError_t f = scratch_free(hist, s);
     if (e == cudaSuccess) e = f;
     if (e != cudaSuccess) {
         cudaGetLastError();
