@@ -205,6 +205,8 @@ k_threshold(TGeo g, int ntasks) {
 template <bool V16>
 __global__ void __launch_bounds__(32 * kThrWarps, 3)
 k_threshold_dev(TGeo g, int ntasks, const int32_t *__restrict__ t_dev) {
+    // launched while k_otsu may still run: wait for it before reading t
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int t = *t_dev;
     const uint32_t tc = (uint32_t)min(max(t, 1), 255);
     g.t4 = (256u - tc) * 0x01010101u;
@@ -237,6 +239,8 @@ template <bool V16>
 __global__ void __launch_bounds__(32 * kHistWarps)
 k_grey_hist(const uint8_t *__restrict__ grey, int32_t w, int32_t h, int32_t pitch,
             unsigned long long *__restrict__ hist) {
+    // k_otsu may be placed now; it waits for this grid before reading
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ uint32_t sh[kHistWarps][256];
     for (int i = threadIdx.x; i < kHistWarps * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
@@ -293,6 +297,8 @@ k_grey_hist(const uint8_t *__restrict__ grey, int32_t w, int32_t h, int32_t pitc
 // anywhere.  The first largest t wins; with one grey value v, t = v.
 __global__ void __launch_bounds__(256)
 k_otsu(const unsigned long long *__restrict__ hist, int32_t *__restrict__ t_out) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ unsigned long long n_s[256], s_s[256];
     __shared__ double best_d[256];
     __shared__ int best_t[256];
@@ -468,9 +474,25 @@ extern "C" int me_threshold_edges_otsu(const uint8_t *grey, int32_t w, int32_t h
             k_grey_hist<true><<<hgrid, 32 * kHistWarps, 0, s>>>(grey, w, h, pitch_bytes, hist);
         else
             k_grey_hist<false><<<hgrid, 32 * kHistWarps, 0, s>>>(grey, w, h, pitch_bytes, hist);
-        k_otsu<<<1, 256, 0, s>>>(hist, t_dev);
-        fn<<<grid, 32 * kThrWarps, 0, s>>>(g, ntasks, t_dev);
+        // the choice of t and the threshold pass by programmatic dependent
+        // launch: each is placed while the kernel before it runs, and waits
+        // for it (griddepcontrol.wait) before reading its result
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(1);
+        lc.blockDim = dim3(256);
+        lc.stream = s;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
         e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaLaunchKernelEx(&lc, k_otsu, (const unsigned long long *)hist, t_dev);
+        lc.gridDim = dim3(grid);
+        lc.blockDim = dim3(32 * kThrWarps);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernelEx(&lc, fn, g, ntasks, (const int32_t *)t_dev);
     }
     const cudaError_t f = scratch_free(hist, s);
     if (e == cudaSuccess) e = f;
