@@ -80,7 +80,8 @@ struct Req {
     size_t pin_off = 0;                // staging: input at in + off, output at out + off
     std::unique_ptr<uint32_t[]> heap;  // input while staging was full
     size_t dev_off = 0;                // device: input at in + off, output at out + off
-    // QUEUED -> ADMITTED under qmu, then DONE or FAILED under the shard;
+    // QUEUED -> ADMITTED under dev_mu (the engine has taken the request off
+    // the queue then), then DONE or FAILED under the shard;
     // atomic so that a poller may watch it without the lock
     std::atomic<State> state{QUEUED};
     bool cancelled = false;            // under qmu and the shard
@@ -207,11 +208,20 @@ struct me_server {
         } while (!freed.compare_exchange_weak(h, r, std::memory_order_release,
                                               std::memory_order_relaxed));
     }
-    void drain_freed() {               // caller holds qmu
-        Req *r = freed.exchange(nullptr, std::memory_order_acquire);
+    // Give the staging of the requests on the freed list back (caller holds
+    // qmu) and return the list, whose requests the caller deletes once it
+    // has let go of qmu (they were allocated by other threads, whose heap
+    // arenas a delete may have to lock).
+    Req *drain_freed() {
+        Req *head = freed.exchange(nullptr, std::memory_order_acquire);
+        for (Req *r = head; r != nullptr; r = r->next_free)
+            if (r->pinned) pin_alloc.release(r->pin_off, r->span);
+        return head;
+    }
+    static void delete_list(Req *r) {
         while (r) {
             Req *n = r->next_free;
-            free_req(r);
+            delete r;
             r = n;
         }
     }
@@ -324,28 +334,47 @@ struct me_server {
     // Engine thread: admission and launches.
     enum Blocked { NOTHING, EMPTY, NOT_COPIED, HEAP, NO_SLOT, NO_MEMORY };
 
-    // Admit a batch from the head of the queue into b (caller holds qmu).
-    Blocked admit(Batch *b) {
+    // Admit a batch from the head of the queue into b.  lk holds qmu on
+    // entry and on return; the ready requests at the head are taken off the
+    // queue under it, and their device memory is given with it released
+    // (submitters are not held up meanwhile).  Those that do not fit go back
+    // to the head of the queue, in order.
+    Blocked admit(Batch *b, std::unique_lock<std::mutex> &lk) {
         if (queue.empty()) return EMPTY;
         Req *f = queue.front();
         if (!f->pinned) return HEAP;
         if (!f->copied.load()) return NOT_COPIED;
-        std::lock_guard<std::mutex> dl(dev_mu);
-        if ((int)inflight.size() >= cfg.max_inflight) return NO_SLOT;
-        if (!new_batch(b)) return NO_SLOT;
-        const auto now = Clock::now();
-        while (!queue.empty() && (int)b->reqs.size() < cfg.max_batch) {
+        {
+            std::lock_guard<std::mutex> dl(dev_mu);
+            if ((int)inflight.size() >= cfg.max_inflight) return NO_SLOT;
+            if (!new_batch(b)) return NO_SLOT;
+        }
+        std::vector<Req *> &take = b->reqs;
+        while (!queue.empty() && (int)take.size() < cfg.max_batch) {
             Req *r = queue.front();
             if (!r->pinned || !r->copied.load()) break;
-            size_t off;
-            if (!dev_alloc.alloc_next(r->span, &off)) break;   // wait for memory
-            r->dev_off = off;
-            r->state = ADMITTED;
-            r->t_admit = now;
             queue.pop_front();
-            b->reqs.push_back(r);
+            take.push_back(r);
         }
-        if (b->reqs.empty()) {
+        lk.unlock();
+        size_t k = 0;
+        {
+            std::lock_guard<std::mutex> dl(dev_mu);
+            const auto now = Clock::now();
+            for (; k < take.size(); ++k) {
+                Req *r = take[k];
+                size_t off;
+                if (!dev_alloc.alloc_next(r->span, &off)) break;   // wait for memory
+                r->dev_off = off;
+                r->t_admit = now;
+                r->state = ADMITTED;
+            }
+        }
+        lk.lock();
+        for (size_t j = take.size(); j-- > k;) queue.push_front(take[j]);
+        take.resize(k);
+        if (take.empty()) {
+            std::lock_guard<std::mutex> dl(dev_mu);
             spare.push_back(std::move(*b));
             return NO_MEMORY;
         }
@@ -357,11 +386,15 @@ struct me_server {
         std::unique_lock<std::mutex> lk(qmu);
         for (;;) {
             const uint64_t seq = wake_seq.load();
-            drain_freed();
+            if (Req *dead = drain_freed()) {
+                lk.unlock();
+                delete_list(dead);
+                lk.lock();
+            }
             stage_heap_requests(lk);
             if (stop) break;
             Batch b;
-            const Blocked why = admit(&b);
+            const Blocked why = admit(&b, lk);
             if (why == NOTHING) {
                 lk.unlock();
                 int64_t nc = 0;
@@ -382,7 +415,7 @@ struct me_server {
             }
             // state what is awaited, then look again: a waker changes its
             // state first and reads engine_waiting / waits_for after
-            Req *f = why == NOT_COPIED ? queue.front() : nullptr;
+            Req *f = why == NOT_COPIED && !queue.empty() ? queue.front() : nullptr;
             waits_for.store(f);
             engine_waiting.store(true);
             const bool changed = wake_seq.load() != seq || (f && f->copied.load());
@@ -471,6 +504,10 @@ void destroy(me_server *s) {
         if (st) cudaStreamDestroy(st);
     for (auto &sh : s->shards)
         for (auto &kv : sh.map) delete kv.second;
+    // cancelled requests the engine put back on the queue after close
+    // emptied it are in no map
+    for (Req *r : s->queue)
+        if (r->cancelled) delete r;
     for (Req *r = s->freed.exchange(nullptr); r != nullptr;) {
         Req *n = r->next_free;
         delete r;
@@ -579,11 +616,12 @@ int me_serve_submit(me_server *s, const uint32_t *host_img, int32_t w, int32_t h
     r->span = (r->bytes + kAlign - 1) / kAlign * kAlign;
     r->t_submit = Clock::now();
     Req *p = r.get();
+    Req *dead = nullptr;
     {
         std::lock_guard<std::mutex> lk(s->qmu);
         if (s->closing) return ME_ERR_CLOSED;
         if (p->span > s->dev_half || p->span > s->pin_half) return ME_ERR_BUDGET;
-        s->drain_freed();
+        dead = s->drain_freed();
         p->pinned = s->pin_alloc.alloc_next(p->span, &p->pin_off);
         p->ticket = s->next_ticket++;
         if (p->pinned) {
@@ -594,6 +632,7 @@ int me_serve_submit(me_server *s, const uint32_t *host_img, int32_t w, int32_t h
             if (s->queue.size() == 1 && s->engine_waiting.load()) s->waits_for.store(p);
         }
     }
+    me_server::delete_list(dead);
     if (!p->pinned) {
         p->heap.reset(new (std::nothrow) uint32_t[p->bytes / 4]);
         if (!p->heap) return ME_ERR_NOMEM;      // p was never queued
@@ -662,8 +701,11 @@ int me_serve_cancel(me_server *s, uint64_t ticket) {
     Req *r = it->second;
     if (r->waiter != nullptr) return ME_ERR_ARG;   // a poll is waiting for it
     sh.map.erase(it);
-    if (r->state == QUEUED) {
-        s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+    const auto qit = std::find(s->queue.begin(), s->queue.end(), r);
+    if (r->state == QUEUED && qit == s->queue.end()) {
+        r->cancelled = true;                // being admitted: freed when its batch retires
+    } else if (r->state == QUEUED) {
+        s->queue.erase(qit);
         if (r->open) {
             s->free_req(r);                 // reserved, never committed
         } else if (!r->copied.load()) {
@@ -698,17 +740,23 @@ int me_serve_reserve(me_server *s, int32_t w, int32_t h, int32_t stride_words,
     r->t_submit = Clock::now();
     r->open = true;
     Req *p = r.get();
+    Req *dead = nullptr;
+    bool room = false;
     {
         std::lock_guard<std::mutex> lk(s->qmu);
         if (s->closing) return ME_ERR_CLOSED;
         if (p->span > s->dev_half || p->span > s->pin_half) return ME_ERR_BUDGET;
-        s->drain_freed();
-        if (!s->pin_alloc.alloc_next(p->span, &p->pin_off)) return ME_PENDING;
-        p->pinned = true;
-        p->ticket = s->next_ticket++;
-        s->queue.push_back(p);
-        if (s->queue.size() == 1 && s->engine_waiting.load()) s->waits_for.store(p);
+        dead = s->drain_freed();
+        room = s->pin_alloc.alloc_next(p->span, &p->pin_off);
+        if (room) {
+            p->pinned = true;
+            p->ticket = s->next_ticket++;
+            s->queue.push_back(p);
+            if (s->queue.size() == 1 && s->engine_waiting.load()) s->waits_for.store(p);
+        }
     }
+    me_server::delete_list(dead);
+    if (!room) return ME_PENDING;
     {
         Shard &sh = s->shard(p->ticket);
         std::lock_guard<std::mutex> sl(sh.mu);
