@@ -548,7 +548,10 @@ def serve_leg(lib_mod, n_requests=100000, loads=(0.25, 0.5, 0.8, 0.95), seed=0):
     # the server takes two threads (engine, completion); the rest drive it
     closed_clients = open_clients = max(2, min(14, cores - 2))
     window = 16
-    cfg = dict(hbm_budget_bytes=8 << 30, staging_bytes=1 << 30, max_inflight=4,
+    # 4 GiB of pinned staging: room for about 20,000 requests of this mix in
+    # flight, so that an offered load near the saturated rate shows as a
+    # backlog (latency) rather than as requests spilling into heap memory
+    cfg = dict(hbm_budget_bytes=8 << 30, staging_bytes=4 << 30, max_inflight=4,
                max_batch=512, tick_us=0)
     srv = lib_mod.Server(**cfg)
     px = sum(im.pixels for im in reqs)
