@@ -202,8 +202,11 @@ k_inplace(IpGeo g) {
 template <bool V16>
 __global__ void __launch_bounds__(256)
 k_seams(const uint32_t *img, uint32_t *seam, int32_t stride, int32_t band_rows) {
-    // the band kernel may be scheduled now; it waits for this grid to end
-    // before it reads anything
+    // launched while the kernel before it on the stream may still run (an
+    // earlier call's bands, possibly on this image): wait for it to end
+    // before reading; the band kernel may be scheduled now, and it waits
+    // for this grid to end before it reads anything
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const size_t words = 2 * (size_t)stride;
     const uint32_t *src = img + ((size_t)(blockIdx.x + 1) * band_rows - 1) * (size_t)stride;
@@ -327,11 +330,20 @@ extern "C" int me_edges_inplace(uint32_t *img, int32_t w, int32_t h, int32_t str
             return record_cuda(e);
         }
         g.seam = seam;
-        if (geo.vec16)
-            k_seams<true><<<g.nbands - 1, 256, 0, s>>>(img, seam, stride_words, g.band_rows);
-        else
-            k_seams<false><<<g.nbands - 1, 256, 0, s>>>(img, seam, stride_words, g.band_rows);
-        e = cudaGetLastError();
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(g.nbands - 1);
+        lc.blockDim = dim3(256);
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        const uint32_t *cimg = img;
+        e = geo.vec16 ? cudaLaunchKernelEx(&lc, k_seams<true>, cimg, seam, stride_words,
+                                           g.band_rows)
+                      : cudaLaunchKernelEx(&lc, k_seams<false>, cimg, seam, stride_words,
+                                           g.band_rows);
     }
     if (e == cudaSuccess) {
         // rows of up to 1024 columns: a 12-row ring, 4 rows per barrier;
