@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include <mutex>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -145,6 +146,35 @@ inline int threshold_band(int64_t ncb, int32_t h, int64_t resident_warps) {
 }
 
 // ---------------------------------------------------------------- helpers
+// Kernels launched by programmatic dependent launch open with this: the
+// launch may be placed while the kernel before it on the stream still
+// runs, so wait for that kernel (and its memory) before the first global
+// access, then let the next launch be placed during this one's tail.  Both
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+#if defined(__CUDA_ARCH__)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+// Launch `kernel` on s with programmatic stream serialisation allowed.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
 // (inline: a batch plan runs them once per image on every call)
 int record_cuda(cudaError_t e);         // remembers e, returns ME_ERR_CUDA
 int check_device_ptr(const void *p);    // ME_OK or ME_ERR_ARG / ME_ERR_CUDA

@@ -197,6 +197,7 @@ __device__ __forceinline__ void thr_run(const TGeo &g, int ntasks) {
 template <bool V16, int MODE>
 __global__ void __launch_bounds__(32 * kThrWarps, 3)
 k_threshold(TGeo g, int ntasks) {
+    pdl_enter();
     thr_run<V16, MODE>(g, ntasks);
 }
 
@@ -427,8 +428,9 @@ extern "C" int me_threshold_edges(const uint8_t *grey, int32_t w, int32_t h, int
     int ntasks = 0;
     unsigned grid = 0;
     if ((rc = thr_grid(reinterpret_cast<const void *>(fn), &g, &ntasks, &grid)) != ME_OK) return rc;
-    fn<<<grid, 32 * kThrWarps, 0, (cudaStream_t)stream>>>(g, ntasks);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_pdl(fn, dim3(grid), dim3(32 * kThrWarps), 0,
+                                     (cudaStream_t)stream, g, ntasks);
+    if (e != cudaSuccess) cudaGetLastError();
     return e == cudaSuccess ? ME_OK : record_cuda(e);
 }
 

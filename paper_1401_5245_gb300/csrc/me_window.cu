@@ -17,6 +17,7 @@ namespace me {
 template <int VW, int RPT, int MODE, int VEC>
 __global__ void __launch_bounds__(512)
 k_window(Geo g, Outs o, int ntasks) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * (unsigned)blockDim.x) >> 5);
@@ -81,8 +82,10 @@ cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
         grid = std::min<int64_t>(grid, (int64_t)di.sm_count * per_sm);
     }
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, INT32_MAX));
-    fn<<<(unsigned)grid, threads, 0, s>>>(g, o, (int)ntasks);
-    return cudaGetLastError();
+    const cudaError_t e = launch_pdl(fn, dim3((unsigned)grid), dim3(threads), 0, s, g, o,
+                                     (int)ntasks);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
 }
 
 // ------------------------------------------------------------- batch
