@@ -325,3 +325,102 @@ def test_load_generator_zero_copy_every_result_is_the_oracles(pool):
     assert r["errors"] == 0 and r["mismatches"] == 0
     assert r2["errors"] == 0
     assert st["completed"] == 2 * len(reqs)
+
+
+def test_random_interleaving_of_every_call(pool):
+    """Six threads each run a random mix of copying and zero-copy submits,
+    polls with random timeouts (0, short, unlimited), views and releases,
+    and cancels of their own requests, against a budget and a staging pool
+    small enough that requests queue for memory and spill into heap
+    memory.  Every result collected equals the oracle's; the server's
+    counters add up; close drains what is left."""
+    want = {id(im): oracle_words(im) for im in pool}
+    page = max(pool, key=lambda im: im.packed_bytes)
+    span = (page.packed_bytes + 255) // 256 * 256
+    srv = _lib.Server(hbm_budget_bytes=6 * span, staging_bytes=8 * span, max_inflight=2,
+                      max_batch=5, tick_us=0)
+    errs, counts = [], []
+
+    def worker(seed):
+        g = np.random.default_rng(seed)
+        live = []          # (ticket, image, zero_copy)
+        done = cancelled = 0
+        try:
+            for _ in range(150):
+                op = g.random()
+                if op < 0.45 or not live:
+                    im = pool[int(g.integers(0, len(pool)))]
+                    if g.random() < 0.5:
+                        rc, t = srv.submit(im.words, im.w, im.h, im.stride_words, im.boundary)
+                        assert rc == 0, _lib.status_string(rc)
+                        live.append((t, im, False))
+                    else:
+                        rc, t, dst = srv.reserve(im.w, im.h, im.stride_words, im.boundary)
+                        if rc == _lib.C["ME_PENDING"]:
+                            continue
+                        assert rc == 0, _lib.status_string(rc)
+                        dst[...] = im.words
+                        assert srv.commit(t) == 0
+                        live.append((t, im, True))
+                elif op < 0.9:
+                    k = int(g.integers(0, len(live)))
+                    t, im, zc = live[k]
+                    # no unlimited wait here: a request in heap memory waits
+                    # for staging that other threads' uncollected results hold
+                    timeout = int(g.choice([0, 200, 5000]))
+                    if zc or g.random() < 0.3:
+                        rc, tm, view = srv.poll_view(t, im.h, im.stride_words, timeout)
+                        if rc in (_lib.C["ME_PENDING"], _lib.C["ME_TIMEOUT"]):
+                            continue
+                        assert rc == 0, _lib.status_string(rc)
+                        assert np.array_equal(view, want[id(im)])
+                        assert srv.release(t) == 0
+                    else:
+                        res = np.empty_like(im.words)
+                        rc, tm = srv.poll(t, res, timeout)
+                        if rc in (_lib.C["ME_PENDING"], _lib.C["ME_TIMEOUT"]):
+                            continue
+                        assert rc == 0, _lib.status_string(rc)
+                        assert np.array_equal(res, want[id(im)])
+                    live.pop(k)
+                    done += 1
+                else:
+                    k = int(g.integers(0, len(live)))
+                    assert srv.cancel(live[k][0]) == 0
+                    live.pop(k)
+                    cancelled += 1
+            # collect the rest, whatever is ready first, so that the staging
+            # of collected results lets the waiting requests in
+            import time
+            deadline = time.monotonic() + 60
+            while live:
+                assert time.monotonic() < deadline, "requests never finished"
+                keep = []
+                for t, im, zc in live:
+                    res = np.empty_like(im.words)
+                    rc, _ = srv.poll(t, res, 0)
+                    if rc == _lib.C["ME_PENDING"]:
+                        keep.append((t, im, zc))
+                        continue
+                    assert rc == 0, _lib.status_string(rc)
+                    assert np.array_equal(res, want[id(im)])
+                    done += 1
+                if len(keep) == len(live):
+                    time.sleep(1e-4)
+                live = keep
+            counts.append((done, cancelled))
+        except Exception as e:   # noqa: BLE001
+            errs.append(e)
+
+    ths = [threading.Thread(target=worker, args=(100 + k,)) for k in range(6)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    try:
+        assert not errs, errs
+        st = srv.stats()
+        assert st["submitted"] == sum(d + c for d, c in counts)
+        assert st["peak_bytes"] <= 6 * span
+    finally:
+        assert srv.close(-1) == 0
