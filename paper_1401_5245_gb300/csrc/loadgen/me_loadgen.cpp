@@ -126,7 +126,50 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
             while (!go.load(std::memory_order_acquire)) std::this_thread::yield();
             Clock::time_point last = t0;
             int64_t next = c;
+            // Take the oldest result; false when it is not ready within
+            // timeout_us (0: not at all).
+            auto collect_oldest = [&](int64_t timeout_us) {
+                me_timing tm{};
+                const Out o = out.front();
+                const uint32_t *view = nullptr;
+                const int rc = zero_copy
+                                   ? me_serve_poll_view(srv, o.ticket, timeout_us, &view, &tm)
+                                   : me_serve_poll(srv, o.ticket, scratch.data(), timeout_us, &tm);
+                if (rc == ME_PENDING || rc == ME_TIMEOUT) return false;
+                out.pop_front();
+                if (rc != ME_OK) {
+                    fail(rc);
+                    if (zero_copy) me_serve_release(srv, o.ticket);
+                    last = Clock::now();
+                    return true;
+                }
+                const me_load_item &it = items[o.i];
+                const size_t bytes = (size_t)it.h * (size_t)it.stride_words * 4;
+                const uint32_t *got = zero_copy ? view : scratch.data();
+                if (it.expect) {
+                    if (std::memcmp(got, it.expect, bytes) != 0) mismatches.fetch_add(1);
+                } else if (zero_copy) {
+                    uint64_t x = 0;
+                    for (size_t k = 0; k < bytes / 4; ++k) x ^= got[k];
+                    checksum.fetch_xor(x, std::memory_order_relaxed);
+                }
+                if (zero_copy) me_serve_release(srv, o.ticket);
+                last = Clock::now();
+                if (latency_us) latency_us[o.i] = us_between(o.from, last);
+                if (server_us) server_us[o.i] = tm.total_us;
+                return true;
+            };
+            // the longest the oldest result may be waited for: until the
+            // next arrival (open loop) or without limit
+            auto patience = [&] {
+                if (!open || next >= n) return (int64_t)-1;
+                return (int64_t)std::max(0.0, us_between(Clock::now(), arrival(next)));
+            };
             while (next < n || !out.empty()) {
+                // whatever has finished is collected first: a client that
+                // falls behind its schedule must not leave results holding
+                // staging while it submits
+                if (!out.empty() && collect_oldest(0)) continue;
                 const auto now = Clock::now();
                 const bool due = next < n && (open ? arrival(next) <= now
                                                    : (int)out.size() < window);
@@ -139,12 +182,10 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                         uint32_t *dst = nullptr;
                         rc = me_serve_reserve(srv, it.w, it.h, it.stride_words, it.boundary,
                                               &tk, &dst);
-                        if (rc == ME_PENDING && !out.empty()) {
-                            // no staging now: collect the oldest result first
-                            goto collect;
-                        }
                         if (rc == ME_PENDING) {
-                            std::this_thread::yield();
+                            // no staging now: wait for the oldest result
+                            if (!out.empty()) collect_oldest(-1);
+                            else std::this_thread::yield();
                             continue;
                         }
                         if (rc == ME_OK) {
@@ -163,40 +204,7 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                     wait_until(arrival(next));
                     continue;
                 }
-            collect : {
-                // the oldest result, waiting no longer than the next arrival
-                int64_t timeout = -1;
-                if (open && next < n)
-                    timeout = (int64_t)std::max(0.0, us_between(Clock::now(), arrival(next)));
-                me_timing tm{};
-                const Out o = out.front();
-                const uint32_t *view = nullptr;
-                const int rc = zero_copy
-                                   ? me_serve_poll_view(srv, o.ticket, timeout, &view, &tm)
-                                   : me_serve_poll(srv, o.ticket, scratch.data(), timeout, &tm);
-                if (rc == ME_PENDING || rc == ME_TIMEOUT) continue;
-                out.pop_front();
-                if (rc != ME_OK) {
-                    fail(rc);
-                    if (zero_copy) me_serve_release(srv, o.ticket);
-                    last = Clock::now();
-                    continue;
-                }
-                const me_load_item &it = items[o.i];
-                const size_t bytes = (size_t)it.h * (size_t)it.stride_words * 4;
-                const uint32_t *got = zero_copy ? view : scratch.data();
-                if (it.expect) {
-                    if (std::memcmp(got, it.expect, bytes) != 0) mismatches.fetch_add(1);
-                } else if (zero_copy) {
-                    uint64_t x = 0;
-                    for (size_t k = 0; k < bytes / 4; ++k) x ^= got[k];
-                    checksum.fetch_xor(x, std::memory_order_relaxed);
-                }
-                if (zero_copy) me_serve_release(srv, o.ticket);
-                last = Clock::now();
-                if (latency_us) latency_us[o.i] = us_between(o.from, last);
-                if (server_us) server_us[o.i] = tm.total_us;
-            }
+                collect_oldest(patience());
             }
             t_last[c] = last;
         });
