@@ -439,7 +439,8 @@ int me_serve_submit(me_server *srv, const uint32_t *host_img, int32_t w,
 /*
  * Collect a result.  Waits up to timeout_us microseconds (0: do not wait,
  * negative: wait without limit) and returns ME_OK with the edge map copied
- * to host_edge (h rows of the request's stride_words, padding written 0)
+ * to host_edge (h rows of the request's stride_words, padding written 0;
+ * NULL for a direct ticket, whose edge map is in its own buffer already)
  * and the timing in *t (may be NULL); ME_PENDING (timeout 0) or
  * ME_TIMEOUT when not ready; ME_ERR_TICKET for an unknown or already
  * collected ticket; ME_ERR_ARG if another thread is already waiting for the
@@ -449,6 +450,24 @@ int me_serve_submit(me_server *srv, const uint32_t *host_img, int32_t w,
  */
 int me_serve_poll(me_server *srv, uint64_t ticket, uint32_t *host_edge,
                   int64_t timeout_us, me_timing *t);
+
+/*
+ * Direct submit, for images that already sit in host memory the GPU can
+ * reach (cudaHostAlloc, cudaHostRegister, torch pin_memory): the batch
+ * kernel reads host_img and writes the edge map into host_edge over the
+ * CPU-GPU link, with no staging copy, no device memory and no copies on the
+ * host or by the copy engines.  Both buffers (h rows of stride_words words,
+ * 4-byte aligned, not overlapping) belong to the caller and must stay valid,
+ * host_img unchanged and host_edge unread, until the ticket is collected
+ * (or, after me_serve_cancel, until me_serve_close).  me_serve_poll of a
+ * direct ticket takes host_edge = NULL (the edge map is already in the
+ * buffer given here); me_serve_poll_view points at that buffer.
+ * ME_ERR_ARG for a buffer the GPU cannot reach.  The HBM budget is not
+ * charged.
+ */
+int me_serve_submit_direct(me_server *srv, const uint32_t *host_img, uint32_t *host_edge,
+                           int32_t w, int32_t h, int32_t stride_words, int32_t boundary,
+                           uint64_t *ticket);
 
 /*
  * Zero-copy submit.  Reserves room for one image (h rows of stride_words

@@ -112,6 +112,8 @@ PROTOTYPES = {
                                        ctypes.POINTER(c_u64)]),
     "me_serve_poll": (ctypes.c_int, [c_vp, c_u64, c_vp, c_i64, ctypes.POINTER(me_timing)]),
     "me_serve_cancel": (ctypes.c_int, [c_vp, c_u64]),
+    "me_serve_submit_direct": (ctypes.c_int, [c_vp, c_vp, c_vp, c_i32, c_i32, c_i32, c_i32,
+                                              ctypes.POINTER(c_u64)]),
     "me_serve_reserve": (ctypes.c_int, [c_vp, c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(c_u64),
                                         ctypes.POINTER(c_vp)]),
     "me_serve_commit": (ctypes.c_int, [c_vp, c_u64]),
@@ -348,6 +350,22 @@ class Server:
     def cancel(self, ticket) -> int:
         return load().me_serve_cancel(self._h, ticket)
 
+    def submit_direct(self, host_img, host_edge, w, h, stride_words, boundary=0):
+        """Direct submit: host_img and host_edge are pinned host buffers (numpy
+        views of pinned tensors, or pointers) the kernel reads and writes."""
+        t = c_u64()
+        pi = host_img.ctypes.data if hasattr(host_img, "ctypes") else int(host_img)
+        po = host_edge.ctypes.data if hasattr(host_edge, "ctypes") else int(host_edge)
+        rc = load().me_serve_submit_direct(self._h, pi, po, w, h, stride_words, boundary,
+                                           ctypes.byref(t))
+        return rc, t.value
+
+    def poll_direct(self, ticket, timeout_us=-1):
+        """Collect a direct ticket (its edge map is in its own buffer)."""
+        tm = me_timing()
+        rc = load().me_serve_poll(self._h, ticket, None, timeout_us, ctypes.byref(tm))
+        return rc, tm
+
     def reserve(self, w, h, stride_words, boundary=0):
         """Zero-copy submit, step 1: (status, ticket, numpy view of the
         staging to write the h x stride_words image into)."""
@@ -435,19 +453,23 @@ def load_loadgen() -> ctypes.CDLL:
             dp = ctypes.POINTER(ctypes.c_double)
             lg.me_load_run.restype = ctypes.c_int
             lg.me_load_run.argtypes = [c_vp, ctypes.POINTER(me_load_item), c_i64, dp, c_i32,
-                                       c_i32, c_i32, dp, dp, ctypes.POINTER(me_load_result)]
+                                       c_i32, c_i32, c_vp, c_i64, c_i32, dp, dp,
+                                       ctypes.POINTER(me_load_result)]
             _loadgen = lg
     return _loadgen
 
 
 def load_run(server: "Server", reqs, expect=None, arrival_s=None, clients=4, window=32,
-             zero_copy=False):
+             zero_copy=False, direct=None):
     """Drive `server` with the requests `reqs` (objects with .words, .w, .h,
     .stride_words, .boundary) from C threads (me_load_run).  expect: None or
     one edge-map array per request to compare with.  arrival_s: None for a
     closed loop of `window` outstanding requests per client, else the
     arrival times in seconds (open loop).  zero_copy: the clients write into
-    reserved staging and read results in place.  Returns wall_s, mismatches,
+    reserved staging and read results in place.  direct: (out_ring, slot_words,
+    slots) -- the requests' images are pinned and the kernel writes each
+    edge map into a slot of the pinned out_ring (`slots` per client).
+    Returns wall_s, mismatches,
     errors, first_error and the per-request latency_us / server_us arrays."""
     import numpy as np
     n = len(reqs)
@@ -466,8 +488,9 @@ def load_run(server: "Server", reqs, expect=None, arrival_s=None, clients=4, win
     res = me_load_result()
     check(load_loadgen().me_load_run(
         server.handle, items, n, arr.ctypes.data_as(dp) if arr is not None else None,
-        clients, window, 1 if zero_copy else 0, lat.ctypes.data_as(dp),
-        srv_us.ctypes.data_as(dp),
+        clients, window, 2 if direct else 1 if zero_copy else 0,
+        direct[0] if direct else None, direct[1] if direct else 0, direct[2] if direct else 0,
+        lat.ctypes.data_as(dp), srv_us.ctypes.data_as(dp),
         ctypes.byref(res)), "me_load_run")
     return {"wall_s": res.wall_s, "mismatches": res.mismatches, "errors": res.errors,
             "first_error": res.first_error, "latency_us": lat, "server_us": srv_us}

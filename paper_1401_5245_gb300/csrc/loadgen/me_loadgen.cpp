@@ -11,10 +11,13 @@
 // from the submit call (closed loop) to the return of the poll that
 // delivered the result, so a client or server that falls behind its
 // schedule shows in it.  Every result can be compared with the edge map it
-// must equal.  With zero_copy the clients use the server's zero-copy calls:
-// each writes its image straight into the staging it reserved and reads the
-// edge map where the server left it (an XOR over its words stands for the
-// client consuming it), instead of one copy in and one copy out.
+// must equal.  Three ways to hand requests over (mode): 0, me_serve_submit
+// and me_serve_poll (one copy in, one copy out); 1, the zero-copy calls
+// (each client writes its image straight into the staging it reserved and
+// reads the edge map where the server left it); 2, me_serve_submit_direct
+// (the images already sit in host memory the GPU reaches, and each client
+// has a ring of such output slots the kernel writes into).  In modes 1 and 2
+// an XOR over the edge map's words stands for the client consuming it.
 //
 // Not part of libme's C ABI; bench.py and the serving tests load it.
 #include <algorithm>
@@ -71,9 +74,12 @@ typedef struct me_load_result {
 
 /*
  * Run n requests through srv.  Request i goes to client i % clients.
- * zero_copy: submit by me_serve_reserve / me_serve_commit and collect by
- * me_serve_poll_view / me_serve_release (else me_serve_submit and
- * me_serve_poll).
+ * mode: 0 me_serve_submit / me_serve_poll; 1 me_serve_reserve /
+ * me_serve_commit and me_serve_poll_view / me_serve_release; 2
+ * me_serve_submit_direct into out_ring (slots of slot_words words, `slots`
+ * per client, client c taking slots c * slots .. c * slots + slots - 1;
+ * the images and the ring must be memory the GPU reaches) and me_serve_poll
+ * with no buffer.  A client holds at most `slots` direct requests.
  * arrival_us: NULL for a closed loop (each client keeps up to `window`
  * requests outstanding), else the arrival time of each request in
  * microseconds from the start (open loop; window is ignored).
@@ -83,13 +89,14 @@ typedef struct me_load_result {
  * requests are counted in *res.
  */
 int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
-                const double *arrival_us, int32_t clients, int32_t window,
-                int32_t zero_copy, double *latency_us, double *server_us,
-                me_load_result *res) {
+                const double *arrival_us, int32_t clients, int32_t window, int32_t mode,
+                uint32_t *out_ring, int64_t slot_words, int32_t slots,
+                double *latency_us, double *server_us, me_load_result *res) {
     if (srv == nullptr || items == nullptr || n <= 0 || clients < 1 || res == nullptr ||
-        (arrival_us == nullptr && window < 1))
+        (arrival_us == nullptr && window < 1) || mode < 0 || mode > 2 ||
+        (mode == 2 && (out_ring == nullptr || slots < 1 || slot_words < 1)))
         return ME_ERR_ARG;
-    std::memset(res, 0, sizeof(*res));
+    const bool zero_copy = mode == 1, direct = mode == 2;
     std::atomic<int64_t> mismatches{0}, errors{0};
     std::atomic<uint64_t> checksum{0};
     std::atomic<int32_t> first_error{0};
@@ -101,6 +108,8 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
     size_t max_bytes = 0;
     for (int64_t i = 0; i < n; ++i)
         max_bytes = std::max(max_bytes, (size_t)items[i].h * (size_t)items[i].stride_words * 4);
+    if (direct && max_bytes > (size_t)slot_words * 4) return ME_ERR_ARG;   // a slot too small
+    std::memset(res, 0, sizeof(*res));
 
     std::atomic<int> ready{0};
     std::atomic<bool> go{false};
@@ -119,7 +128,9 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                 int64_t i;
                 uint64_t ticket;
                 Clock::time_point from;
+                uint32_t *slot;        // direct: the output slot
             };
+            int64_t next_slot = 0;
             std::deque<Out> out;
             prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);   // 1 us sleep precision
             ready.fetch_add(1);
@@ -132,9 +143,10 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                 me_timing tm{};
                 const Out o = out.front();
                 const uint32_t *view = nullptr;
-                const int rc = zero_copy
-                                   ? me_serve_poll_view(srv, o.ticket, timeout_us, &view, &tm)
-                                   : me_serve_poll(srv, o.ticket, scratch.data(), timeout_us, &tm);
+                const int rc = zero_copy ? me_serve_poll_view(srv, o.ticket, timeout_us, &view, &tm)
+                               : direct  ? me_serve_poll(srv, o.ticket, nullptr, timeout_us, &tm)
+                                         : me_serve_poll(srv, o.ticket, scratch.data(), timeout_us,
+                                                         &tm);
                 if (rc == ME_PENDING || rc == ME_TIMEOUT) return false;
                 out.pop_front();
                 if (rc != ME_OK) {
@@ -145,10 +157,10 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                 }
                 const me_load_item &it = items[o.i];
                 const size_t bytes = (size_t)it.h * (size_t)it.stride_words * 4;
-                const uint32_t *got = zero_copy ? view : scratch.data();
+                const uint32_t *got = zero_copy ? view : direct ? o.slot : scratch.data();
                 if (it.expect) {
                     if (std::memcmp(got, it.expect, bytes) != 0) mismatches.fetch_add(1);
-                } else if (zero_copy) {
+                } else if (zero_copy || direct) {
                     uint64_t x = 0;
                     for (size_t k = 0; k < bytes / 4; ++k) x ^= got[k];
                     checksum.fetch_xor(x, std::memory_order_relaxed);
@@ -171,14 +183,22 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                 // staging while it submits
                 if (!out.empty() && collect_oldest(0)) continue;
                 const auto now = Clock::now();
+                // a direct client also needs a free output slot
                 const bool due = next < n && (open ? arrival(next) <= now
-                                                   : (int)out.size() < window);
+                                                   : (int)out.size() < window) &&
+                                 (!direct || (int)out.size() < slots);
                 if (due) {
                     const me_load_item &it = items[next];
                     const auto from = open ? arrival(next) : Clock::now();
                     uint64_t tk = 0;
                     int rc;
-                    if (zero_copy) {
+                    uint32_t *slot = nullptr;
+                    if (direct) {
+                        slot = out_ring + ((int64_t)c * slots + next_slot % slots) * slot_words;
+                        ++next_slot;
+                        rc = me_serve_submit_direct(srv, it.img, slot, it.w, it.h,
+                                                    it.stride_words, it.boundary, &tk);
+                    } else if (zero_copy) {
                         uint32_t *dst = nullptr;
                         rc = me_serve_reserve(srv, it.w, it.h, it.stride_words, it.boundary,
                                               &tk, &dst);
@@ -196,7 +216,7 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                         rc = me_serve_submit(srv, it.img, it.w, it.h, it.stride_words,
                                              it.boundary, &tk);
                     }
-                    if (rc == ME_OK) out.push_back({next, tk, from}); else fail(rc);
+                    if (rc == ME_OK) out.push_back({next, tk, from, slot}); else fail(rc);
                     next += clients;
                     continue;
                 }
@@ -204,7 +224,8 @@ int me_load_run(me_server *srv, const me_load_item *items, int64_t n,
                     wait_until(arrival(next));
                     continue;
                 }
-                collect_oldest(patience());
+                // every output slot taken: the oldest result frees one
+                collect_oldest(direct && (int)out.size() >= slots ? -1 : patience());
             }
             t_last[c] = last;
         });

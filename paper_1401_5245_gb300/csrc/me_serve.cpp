@@ -74,7 +74,8 @@ struct Req {
     uint64_t ticket = 0;
     int32_t w = 0, h = 0, stride = 0, boundary = 0;
     size_t bytes = 0, span = 0;        // packed size; rounded to kAlign
-    bool pinned = false;               // input is in staging (else in heap); qmu
+    bool pinned = false;               // input is in staging (else in heap), or
+                                       // a direct request; qmu
     std::atomic<bool> copied{false};   // the input copy into staging is done
     Req *next_free = nullptr;          // link in the server's list of freed requests
     size_t pin_off = 0;                // staging: input at in + off, output at out + off
@@ -86,6 +87,12 @@ struct Req {
     std::atomic<State> state{QUEUED};
     bool cancelled = false;            // under qmu and the shard
     bool open = false;                 // reserved, not yet committed (qmu and the shard)
+    // direct request: the kernel reads host_in and writes host_out, the
+    // caller's own host buffers, over the CPU-GPU link (no staging, no
+    // device memory, no copies)
+    const uint32_t *host_in = nullptr;
+    uint32_t *host_out = nullptr;
+    bool direct() const { return host_out != nullptr; }
     // the condition the poller waiting for this request sleeps on (only that
     // poller is woken when the request's batch retires); under the shard
     std::condition_variable *waiter = nullptr;
@@ -109,8 +116,12 @@ template <class F>
 void for_each_run(const std::vector<Req *> &reqs, F &&f) {
     size_t i = 0;
     while (i < reqs.size()) {
+        if (reqs[i]->direct()) {       // nothing to copy
+            ++i;
+            continue;
+        }
         size_t j = i;
-        while (j + 1 < reqs.size() &&
+        while (j + 1 < reqs.size() && !reqs[j + 1]->direct() &&
                reqs[j + 1]->pin_off == reqs[j]->pin_off + reqs[j]->span &&
                reqs[j + 1]->dev_off == reqs[j]->dev_off + reqs[j]->span)
             ++j;
@@ -196,7 +207,7 @@ struct me_server {
 
     // ------------------------------------------------------------------
     void free_req(Req *r) {            // caller holds qmu
-        if (r->pinned) pin_alloc.release(r->pin_off, r->span);
+        if (r->pinned && !r->direct()) pin_alloc.release(r->pin_off, r->span);
         delete r;
     }
 
@@ -215,7 +226,7 @@ struct me_server {
     Req *drain_freed() {
         Req *head = freed.exchange(nullptr, std::memory_order_acquire);
         for (Req *r = head; r != nullptr; r = r->next_free)
-            if (r->pinned) pin_alloc.release(r->pin_off, r->span);
+            if (r->pinned && !r->direct()) pin_alloc.release(r->pin_off, r->span);
         return head;
     }
     static void delete_list(Req *r) {
@@ -302,10 +313,14 @@ struct me_server {
                 e = cudaMemcpyAsync(dev_in(a), pin_in(a), n, cudaMemcpyHostToDevice, s_h2d);
             ++nc;
         });
-        for (Req *r : b.reqs)
-            descs.push_back({reinterpret_cast<const uint32_t *>(dev_in(r)),
-                             reinterpret_cast<uint32_t *>(dev_out(r)), r->w, r->h, r->stride,
-                             r->boundary});
+        for (Req *r : b.reqs) {
+            if (r->direct())
+                descs.push_back({r->host_in, r->host_out, r->w, r->h, r->stride, r->boundary});
+            else
+                descs.push_back({reinterpret_cast<const uint32_t *>(dev_in(r)),
+                                 reinterpret_cast<uint32_t *>(dev_out(r)), r->w, r->h, r->stride,
+                                 r->boundary});
+        }
         if (e == cudaSuccess) e = cudaEventRecord(b.up, s_h2d);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s_comp, b.up, 0);
         if (e == cudaSuccess) {
@@ -363,9 +378,11 @@ struct me_server {
             const auto now = Clock::now();
             for (; k < take.size(); ++k) {
                 Req *r = take[k];
-                size_t off;
-                if (!dev_alloc.alloc_next(r->span, &off)) break;   // wait for memory
-                r->dev_off = off;
+                if (!r->direct()) {
+                    size_t off;
+                    if (!dev_alloc.alloc_next(r->span, &off)) break;   // wait for memory
+                    r->dev_off = off;
+                }
                 r->t_admit = now;
                 r->state = ADMITTED;
             }
@@ -454,7 +471,8 @@ struct me_server {
                 std::lock_guard<std::mutex> dl(dev_mu);
                 Batch &b = inflight.front();
                 if (b.failed) q = cudaErrorLaunchFailure;
-                for (Req *r : b.reqs) dev_alloc.release(r->dev_off, r->span);
+                for (Req *r : b.reqs)
+                    if (!r->direct()) dev_alloc.release(r->dev_off, r->span);
                 reqs.swap(b.reqs);
                 spare.push_back(std::move(b));
                 inflight.pop_front();
@@ -662,12 +680,13 @@ int me_serve_submit(me_server *s, const uint32_t *host_img, int32_t w, int32_t h
 
 int me_serve_poll(me_server *s, uint64_t ticket, uint32_t *host_edge, int64_t timeout_us,
                   me_timing *t) {
-    if (s == nullptr || host_edge == nullptr) return ME_ERR_ARG;
+    if (s == nullptr) return ME_ERR_ARG;
     Shard &sh = s->shard(ticket);
     std::unique_lock<std::mutex> sl(sh.mu);
     auto it = sh.map.find(ticket);
     if (it == sh.map.end()) return ME_ERR_TICKET;
     Req *r = it->second;
+    if (host_edge == nullptr && !r->direct()) return ME_ERR_ARG;
     if (!finished(r)) {
         const int rc = wait_finished(sl, r, timeout_us);
         if (rc != ME_OK) return rc;
@@ -677,7 +696,10 @@ int me_serve_poll(me_server *s, uint64_t ticket, uint32_t *host_edge, int64_t ti
     sl.unlock();
     const bool ok = r->state == DONE;
     if (ok) {
-        std::memcpy(host_edge, s->pin_out(r), r->bytes);
+        if (!r->direct())
+            std::memcpy(host_edge, s->pin_out(r), r->bytes);
+        else if (host_edge != nullptr && host_edge != r->host_out)
+            std::memcpy(host_edge, r->host_out, r->bytes);
         if (t) {
             t->queue_us = us_since(r->t_submit, r->t_admit);
             t->device_us = us_since(r->t_admit, r->t_done);
@@ -769,6 +791,60 @@ int me_serve_reserve(me_server *s, int32_t w, int32_t h, int32_t stride_words,
     return ME_OK;
 }
 
+int me_serve_submit_direct(me_server *s, const uint32_t *host_img, uint32_t *host_edge,
+                           int32_t w, int32_t h, int32_t stride_words, int32_t boundary,
+                           uint64_t *ticket) {
+    if (s == nullptr || host_img == nullptr || host_edge == nullptr || ticket == nullptr)
+        return ME_ERR_ARG;
+    if (w <= 0 || h <= 0 || stride_words < (int32_t)(((int64_t)w + 31) / 32) ||
+        (boundary != ME_BOUNDARY_WHITE && boundary != ME_BOUNDARY_BLACK) ||
+        ((uintptr_t)host_img & 3) || ((uintptr_t)host_edge & 3))
+        return ME_ERR_ARG;
+    const size_t bytes = (size_t)h * (size_t)stride_words * 4;
+    if (ranges_overlap(host_img, bytes, host_edge, bytes)) return ME_ERR_ALIAS;
+    // both buffers must be host memory the device can reach (pinned or
+    // registered with CUDA)
+    for (const void *q : {static_cast<const void *>(host_img), static_cast<const void *>(host_edge)}) {
+        cudaPointerAttributes a;
+        const cudaError_t e = cudaPointerGetAttributes(&a, q);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ME_ERR_ARG;
+        }
+        if (a.type != cudaMemoryTypeHost) return ME_ERR_ARG;
+    }
+    std::unique_ptr<Req> r(new (std::nothrow) Req());
+    if (!r) return ME_ERR_NOMEM;
+    r->w = w;
+    r->h = h;
+    r->stride = stride_words;
+    r->boundary = boundary;
+    r->bytes = bytes;
+    r->span = (bytes + kAlign - 1) / kAlign * kAlign;
+    r->host_in = host_img;
+    r->host_out = host_edge;
+    r->pinned = true;                       // ready for admission as it stands
+    r->copied.store(true);
+    r->t_submit = Clock::now();
+    Req *p = r.get();
+    {
+        std::lock_guard<std::mutex> lk(s->qmu);
+        if (s->closing) return ME_ERR_CLOSED;
+        p->ticket = s->next_ticket++;
+        Shard &sh = s->shard(p->ticket);
+        {
+            std::lock_guard<std::mutex> sl(sh.mu);
+            sh.map[p->ticket] = p;
+        }
+        s->queue.push_back(p);
+        r.release();
+        ++s->submitted;
+        *ticket = p->ticket;
+        if (s->queue.front() == p) s->wake_engine_locked();
+    }
+    return ME_OK;
+}
+
 int me_serve_commit(me_server *s, uint64_t ticket) {
     if (s == nullptr) return ME_ERR_ARG;
     Req *p = nullptr;
@@ -797,7 +873,7 @@ int me_serve_poll_view(me_server *s, uint64_t ticket, int64_t timeout_us,
     const int rc = wait_finished(sl, r, timeout_us);
     if (rc != ME_OK) return rc;
     if (r->state == FAILED) return ME_ERR_CUDA;
-    *host_edge = reinterpret_cast<const uint32_t *>(s->pin_out(r));
+    *host_edge = r->direct() ? r->host_out : reinterpret_cast<const uint32_t *>(s->pin_out(r));
     if (t) {
         t->queue_us = us_since(r->t_submit, r->t_admit);
         t->device_us = us_since(r->t_admit, r->t_done);

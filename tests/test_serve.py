@@ -244,8 +244,8 @@ def test_load_generator_open_loop_and_black_boundary(pool):
 def test_load_generator_refuses_bad_arguments():
     lg = _lib.load_loadgen()
     res = _lib.me_load_result()
-    assert lg.me_load_run(None, None, 0, None, 1, 1, 0, None, None, ctypes.byref(res)) == \
-        _lib.C["ME_ERR_ARG"]
+    assert lg.me_load_run(None, None, 0, None, 1, 1, 0, None, 0, 0, None, None,
+                          ctypes.byref(res)) == _lib.C["ME_ERR_ARG"]
 
 
 # ------------------------------------------------------------- zero copy
@@ -424,3 +424,83 @@ def test_random_interleaving_of_every_call(pool):
         assert st["peak_bytes"] <= 6 * span
     finally:
         assert srv.close(-1) == 0
+
+
+# ------------------------------------------------------------ direct submit
+def pinned_copy(words):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(words).view(np.int32)).pin_memory()
+    return t, t.numpy().view(np.uint32)
+
+
+def test_direct_submit_reads_and_writes_the_callers_pinned_buffers(pool):
+    """The kernel reads each image from the caller's pinned buffer and
+    writes the edge map into the caller's pinned output: every one is the
+    oracle's, with copying requests mixed in; unpinned buffers and
+    overlapping ones are refused."""
+    import torch
+    srv = _lib.Server(hbm_budget_bytes=64 << 20, staging_bytes=64 << 20, max_inflight=2,
+                      max_batch=8, tick_us=0)
+    keep = []
+    try:
+        tickets = []
+        for k, im in enumerate(pool):
+            ti, src = pinned_copy(im.words)
+            to, dst = pinned_copy(np.full_like(im.words, 0xA5A5A5A5))
+            keep += [ti, to]
+            rc, t = srv.submit_direct(src, dst, im.w, im.h, im.stride_words, im.boundary)
+            assert rc == 0, _lib.status_string(rc)
+            tickets.append((t, im, dst, True))
+            if k % 3 == 0:       # a copying request in between
+                rc, t2 = srv.submit(im.words, im.w, im.h, im.stride_words, im.boundary)
+                assert rc == 0
+                tickets.append((t2, im, None, False))
+        for t, im, dst, direct in tickets:
+            if direct:
+                rc, tm = srv.poll_direct(t)
+                got = dst
+            else:
+                got = np.empty_like(im.words)
+                rc, tm = srv.poll(t, got, -1)
+            assert rc == 0, _lib.status_string(rc)
+            assert np.array_equal(got, oracle_words(im)), (im.w, im.h, direct)
+        # refused: unpinned memory, overlap
+        im = pool[0]
+        _, src = pinned_copy(im.words)
+        plain = np.empty_like(im.words)
+        assert srv.submit_direct(src, plain, im.w, im.h, im.stride_words)[0] == \
+            _lib.C["ME_ERR_ARG"]
+        assert srv.submit_direct(src, src, im.w, im.h, im.stride_words)[0] == \
+            _lib.C["ME_ERR_ALIAS"]
+    finally:
+        assert srv.close() == 0
+
+
+def test_load_generator_direct_every_result_is_the_oracles(pool):
+    """Direct mode of the load generator: the clients submit pinned images
+    and the kernel writes each edge map into the client's slot of a pinned
+    ring; every result is the oracle's, closed and open loop."""
+    import torch
+    want = [oracle_words(im) for im in pool]
+    pinned = [pinned_copy(im.words) for im in pool]
+    g = np.random.default_rng(9)
+    idx = [int(i) for i in g.integers(0, len(pool), 3000)]
+    reqs = [S.Image(pinned[i][1], pool[i].w, pool[i].h, pool[i].boundary) for i in idx]
+    slot_words = max(im.words.size for im in pool)
+    clients, slots = 4, 8
+    ring = torch.empty(clients * slots * slot_words, dtype=torch.int32).pin_memory()
+    srv = _lib.Server(hbm_budget_bytes=256 << 20, staging_bytes=64 << 20, max_inflight=2,
+                      max_batch=64, tick_us=0)
+    try:
+        r = _lib.load_run(srv, reqs, expect=[want[i] for i in idx], clients=clients,
+                          window=8, direct=(ring.data_ptr(), slot_words, slots))
+        t = np.cumsum(g.exponential(1e-5, len(reqs)))
+        r2 = _lib.load_run(srv, reqs, arrival_s=t, clients=3,
+                           direct=(ring.data_ptr(), slot_words, slots))
+        st = srv.stats()
+    finally:
+        assert srv.close() == 0
+    assert r["errors"] == 0 and r["mismatches"] == 0, r["first_error"]
+    assert r2["errors"] == 0, r2["first_error"]
+    assert st["completed"] == 2 * len(reqs)
+    assert st["copies"] == 0, st        # no staging copy in direct mode
