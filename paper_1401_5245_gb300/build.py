@@ -104,7 +104,7 @@ def build_loadgen(force: bool = False) -> str:
     if not (force or _stale(LOADGEN, deps)):
         return LOADGEN
     tmp = LOADGEN + f".tmp{os.getpid()}"
-    cmd = [cxx(), "-O2", "-std=c++17", "-shared", "-fPIC", "-Wall", "-I", INCLUDE,
+    cmd = [cxx(), "-O3", "-std=c++17", "-shared", "-fPIC", "-Wall", "-I", INCLUDE,
            LOADGEN_SRC, "-o", tmp, "-L", PKG, "-lme", "-Wl,-rpath,$ORIGIN", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

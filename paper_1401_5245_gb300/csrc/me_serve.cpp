@@ -313,6 +313,9 @@ struct me_server {
                 e = cudaMemcpyAsync(dev_in(a), pin_in(a), n, cudaMemcpyHostToDevice, s_h2d);
             ++nc;
         });
+        // a batch of direct requests only has no copies: the kernel and the
+        // done event are all it enqueues
+        const bool copying = nc > 0;
         for (Req *r : b.reqs) {
             if (r->direct())
                 descs.push_back({r->host_in, r->host_out, r->w, r->h, r->stride, r->boundary});
@@ -321,23 +324,26 @@ struct me_server {
                                  reinterpret_cast<uint32_t *>(dev_out(r)), r->w, r->h, r->stride,
                                  r->boundary});
         }
-        if (e == cudaSuccess) e = cudaEventRecord(b.up, s_h2d);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_comp, b.up, 0);
+        if (copying && e == cudaSuccess) e = cudaEventRecord(b.up, s_h2d);
+        if (copying && e == cudaSuccess) e = cudaStreamWaitEvent(s_comp, b.up, 0);
         if (e == cudaSuccess) {
             const int rc = ring->launch(descs.data(), (int)descs.size(), s_comp);
             if (rc != ME_OK) e = cudaErrorLaunchFailure;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(b.kern, s_comp);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_d2h, b.kern, 0);
-        for_each_run(b.reqs, [&](const Req *a, const Req *z) {
-            const size_t n = z->pin_off + z->bytes - a->pin_off;
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(pin_out(a), dev_out(a), n, cudaMemcpyDeviceToHost, s_d2h);
-            ++nc;
-        });
+        if (copying) {
+            if (e == cudaSuccess) e = cudaEventRecord(b.kern, s_comp);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s_d2h, b.kern, 0);
+            for_each_run(b.reqs, [&](const Req *a, const Req *z) {
+                const size_t n = z->pin_off + z->bytes - a->pin_off;
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(pin_out(a), dev_out(a), n, cudaMemcpyDeviceToHost,
+                                        s_d2h);
+                ++nc;
+            });
+        }
         // recorded even after a failure, so that the batch retires once
         // whatever was enqueued has finished
-        const cudaError_t f = cudaEventRecord(b.done, s_d2h);
+        const cudaError_t f = cudaEventRecord(b.done, copying ? s_d2h : s_comp);
         *ncopies = nc;
         if (e != cudaSuccess || f != cudaSuccess) {
             cudaGetLastError();
