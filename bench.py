@@ -442,12 +442,19 @@ def otsu_leg(lib_mod, stream, peak, gate, side=16384):
 
 def unpadded_leg(lib_mod, stream, peak, gate):
     """The uneven batch with stride = ceil(w / 32) (no padding to 16 bytes):
-    rows are not 16-byte groups, so every image takes the 32-bit path."""
+    rows are not 16-byte groups, so the images take 64-bit accesses (even
+    strides) or 32-bit ones (odd strides).  Such batches are of the kind
+    ME_KIND_BATCH_ANY, whose tile shape the autotuner picks on this batch
+    first, as it does for the padded batch's kind."""
     import torch
     from paper_1401_5245_gb300 import synth
     batch = synth.batch(0, N_IMAGES, pad16=False, workers=min(16, os.cpu_count() or 1))
     dev_in, dev_out, _, _, offs = upload_batch(batch, torch.device("cuda", 0))
     descs = descs_for(lib_mod, batch, dev_in, dev_out, offs)
+    t_tune = time.time()
+    cfg = lib_mod.me_autotune(lib_mod.ME_KIND_BATCH_ANY, descs, len(batch), reps=7,
+                              stream=stream)
+    t_tune = time.time() - t_tune
     plan = lib_mod.BatchPlan(descs, len(batch), stream)
     lib_mod.check(plan.run(stream))
     torch.cuda.synchronize()
@@ -458,7 +465,8 @@ def unpadded_leg(lib_mod, stream, peak, gate):
     px = sum(im.pixels for im in batch)
     res = {"gpixel_s": round(px / t / 1e9, 1), "gb_s": round(nbytes / t / 1e9, 1),
            "frac_of_peak": round(nbytes / t / 1e9 / peak, 4), "us": round(t * 1e6, 1),
-           "exact_images_checked": len(sample)}
+           "exact_images_checked": len(sample), "tile_cfg": cfg.as_dict(),
+           "autotune_s": round(t_tune, 1)}
     gate.add(res, "exact", "batch", batch, sample)
     return res
 
@@ -544,6 +552,21 @@ def serve_leg(lib_mod, n_requests=100000, loads=(0.25, 0.5, 0.8, 0.95), seed=0):
         torch.cuda.synchronize()
         alone[id(im)] = yd.cpu().numpy().view(np.uint32).copy()
     expect = [alone[id(im)] for im in reqs]
+    # the autotuner picks the tile shape of the serving batches' kind on a
+    # launch of 32 requests of the mix (device copies), as the batch legs
+    # tune theirs on their own batches
+    tune_reqs = reqs[:32]
+    xs = [torch.from_numpy(im.words.view(np.int32)).cuda() for im in tune_reqs]
+    ys = [torch.empty_like(x) for x in xs]
+    tune_descs = lib_mod.make_descs([(x.data_ptr(), y.data_ptr(), im.w, im.h, im.stride_words,
+                                      im.boundary) for x, y, im in zip(xs, ys, tune_reqs)])
+    tune_kind = (lib_mod.ME_KIND_BATCH_ANY if any(im.stride_words % 4 for im in tune_reqs)
+                 else lib_mod.ME_KIND_BATCH)
+    t_tune = time.time()
+    tuned = lib_mod.me_autotune(tune_kind, tune_descs, len(tune_reqs), reps=20,
+                                stream=torch.cuda.current_stream())
+    t_tune = time.time() - t_tune
+    del xs, ys
     cores = os.cpu_count() or 8
     # the server takes two threads (engine, completion); the rest drive it
     closed_clients = open_clients = max(2, min(14, cores - 2))
@@ -562,7 +585,9 @@ def serve_leg(lib_mod, n_requests=100000, loads=(0.25, 0.5, 0.8, 0.95), seed=0):
               "mean_packed_bytes_each_way": round(nbytes / 2 / n_requests),
               "driver": "libme_loadgen.so (C threads through the public C ABI)",
               "closed_clients": closed_clients, "closed_window": window,
-              "open_clients": open_clients}
+              "open_clients": open_clients,
+              "tile_cfg": dict(kind=tune_kind, autotune_s=round(t_tune, 1),
+                               **tuned.as_dict())}
 
     def point(r, before, after):
         lat, sv = r["latency_us"], r["server_us"]
@@ -1042,7 +1067,8 @@ def run_profile_case(case: str, launches: int, cfg: str | None = None):
     from paper_1401_5245_gb300 import _lib, synth
     lib = _lib.load()
     if cfg:
-        kind = 1 if case.startswith("batch") else 0
+        kind = (_lib.ME_KIND_BATCH_ANY if case == "batch_unpadded"
+                else _lib.ME_KIND_BATCH if case.startswith("batch") else _lib.ME_KIND_SINGLE)
         _lib.check(_lib.me_set_tile_cfg(kind, _lib.me_tile_cfg(*map(int, cfg.split(",")))),
                    "me_set_tile_cfg")
     device = torch.device("cuda", 0)

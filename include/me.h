@@ -336,8 +336,15 @@ int me_edges_batch_host(const uint32_t *host_in, uint32_t *host_out,
 
 /* ---- tile configuration and autotuning --------------------------------- */
 
-#define ME_KIND_SINGLE 0     /* me_edges and its single-image relatives */
-#define ME_KIND_BATCH  1     /* me_edges_batch, plans and the server */
+#define ME_KIND_SINGLE    0  /* me_edges and its single-image relatives */
+#define ME_KIND_BATCH     1  /* me_edges_batch, plans, the host-buffer batch
+                                and the server: batches whose every image
+                                allows 128-bit accesses (both buffers 16-byte
+                                aligned, stride_words % 4 == 0) */
+#define ME_KIND_BATCH_ANY 2  /* the same calls on batches holding at least
+                                one image that does not (the batch kernel
+                                form with 64- and 32-bit accesses, whose best
+                                tile shape differs) */
 
 #define ME_ENGINE_REGS 0     /* rows slide through registers, 128/32-bit loads */
 #define ME_ENGINE_BULK 1     /* row bands staged in shared memory by bulk
@@ -376,7 +383,9 @@ int me_set_tile_cfg(int32_t kind, const me_tile_cfg *cfg);
 /*
  * Time every candidate configuration on the caller's images (device
  * buffers; results are written to their edge buffers) with CUDA events on
- * `stream`, set the fastest for `kind`, and return it in *best.  Each
+ * `stream`, set the fastest for `kind`, and return it in *best.  A batch
+ * sample must be of the batch kind named (ME_ERR_ARG otherwise: its
+ * launches would not use the configurations being timed).  Each
  * candidate runs `reps` calls back to back (steady-state throughput), best
  * of three such runs.  Runs synchronously.  If the environment variable
  * ME_TUNE_CACHE names a file, the choice is also written there and read

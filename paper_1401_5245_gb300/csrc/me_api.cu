@@ -61,17 +61,32 @@ int ceil_log2(int v) {
 
 // ------------------------------------------------------------ tile configs
 static std::mutex g_cfg_mu;
-static me_tile_cfg g_cfg[2] = {
+static me_tile_cfg g_cfg[3] = {
     {ME_ENGINE_REGS, 4, 4, 128, 0, 32, 4, 0},     // single image
-    {ME_ENGINE_REGS, 4, 4, 512, 8, 32, 4, 4},     // batch
+    {ME_ENGINE_REGS, 4, 4, 512, 8, 32, 4, 4},     // batch, 128-bit accesses throughout
+    {ME_ENGINE_REGS, 4, 4, 128, 0, 32, 4, 4},     // batch with narrower accesses
 };
+
+static bool valid_kind(int kind) {
+    return kind == ME_KIND_SINGLE || kind == ME_KIND_BATCH || kind == ME_KIND_BATCH_ANY;
+}
 
 void apply_tune_cache(int kind);
 
 me_tile_cfg tile_cfg(int kind) {
     apply_tune_cache(kind);
     std::lock_guard<std::mutex> lk(g_cfg_mu);
-    return g_cfg[kind == ME_KIND_BATCH ? 1 : 0];
+    return g_cfg[valid_kind(kind) ? kind : ME_KIND_SINGLE];
+}
+
+bool batch_any(const me_desc *descs, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!vec16_ok(descs[i].img, descs[i].edge, descs[i].stride_words)) return true;
+    return false;
+}
+
+me_tile_cfg batch_cfg(const me_desc *descs, int n) {
+    return tile_cfg(batch_any(descs, n) ? ME_KIND_BATCH_ANY : ME_KIND_BATCH);
 }
 
 bool valid_cfg(const me_tile_cfg &c) {
@@ -137,13 +152,13 @@ int me_device_faults(int32_t clear, uint32_t *flags) {
 }
 
 int me_get_tile_cfg(int32_t kind, me_tile_cfg *out) {
-    if (out == nullptr || (kind != ME_KIND_SINGLE && kind != ME_KIND_BATCH)) return ME_ERR_ARG;
+    if (out == nullptr || !valid_kind(kind)) return ME_ERR_ARG;
     *out = tile_cfg(kind);
     return ME_OK;
 }
 
 int me_set_tile_cfg(int32_t kind, const me_tile_cfg *cfg) {
-    if (cfg == nullptr || (kind != ME_KIND_SINGLE && kind != ME_KIND_BATCH)) return ME_ERR_ARG;
+    if (cfg == nullptr || !valid_kind(kind)) return ME_ERR_ARG;
     if (!valid_cfg(*cfg)) return ME_ERR_ARG;
     if (cfg->engine == ME_ENGINE_BULK && !bulk_available()) return ME_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_cfg_mu);

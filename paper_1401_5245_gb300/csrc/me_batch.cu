@@ -213,7 +213,7 @@ int BatchRing::launch(const me_desc *descs, int n, cudaStream_t stream) {
     if (n < 0 || (n > 0 && descs == nullptr)) return ME_ERR_ARG;
     if (n == 0) return ME_OK;
     Setup su;
-    int rc = setup_batch(descs, n, tile_cfg(ME_KIND_BATCH), &su);
+    int rc = setup_batch(descs, n, batch_cfg(descs, n), &su);
     if (rc != ME_OK) return rc;
     std::lock_guard<std::mutex> lk(mu_);
     Slot &slot = slots_[next_];
@@ -314,7 +314,7 @@ int me_batch_plan_create(const me_desc *descs, int32_t n, me_stream_t stream,
     if (out == nullptr || n <= 0 || descs == nullptr) return ME_ERR_ARG;
     *out = nullptr;
     Setup su;
-    int rc = setup_batch(descs, n, tile_cfg(ME_KIND_BATCH), &su);
+    int rc = setup_batch(descs, n, batch_cfg(descs, n), &su);
     if (rc != ME_OK) return rc;
     std::vector<unsigned char> host;
     try {

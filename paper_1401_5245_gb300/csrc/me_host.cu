@@ -263,7 +263,6 @@ extern "C" int me_edges_batch_host(const uint32_t *host_in, uint32_t *host_out,
     if ((e = cudaStreamWaitEvent(p->up, p->start, 0)) != cudaSuccess) return fail_drain(p, fail(e));
     if ((e = upload(0)) != cudaSuccess) return fail_drain(p, fail(e));
 
-    const me_tile_cfg cfg = tile_cfg(ME_KIND_BATCH);
     std::vector<BatchSetup> setups(chunks.size());
     std::vector<size_t> arena_at(chunks.size());
     std::vector<me_desc> descs((size_t)n);     // device-side view of every image
@@ -279,7 +278,8 @@ extern "C" int me_edges_batch_host(const uint32_t *host_in, uint32_t *host_out,
                         reinterpret_cast<uint32_t *>(dout + at_out), m.w, m.h, m.stride_words,
                         m.boundary};
         }
-        if ((rc = setup_batch(&descs[c.first], c.count, cfg, &setups[k])) != ME_OK)
+        if ((rc = setup_batch(&descs[c.first], c.count, batch_cfg(&descs[c.first], c.count),
+                              &setups[k])) != ME_OK)
             return fail_drain(p, rc);
         arena_at[k] = plans;
         plans += (setups[k].arena + 255) / 256 * 256;

@@ -250,6 +250,10 @@ int ceil_log2(int v);
 
 // ------------------------------------------------------- configurations
 me_tile_cfg tile_cfg(int kind);         // current configuration of a kind
+// Some image of the batch cannot take 128-bit accesses (ME_KIND_BATCH_ANY).
+bool batch_any(const me_desc *descs, int n);
+// The configuration of the batch's kind.
+me_tile_cfg batch_cfg(const me_desc *descs, int n);
 bool valid_cfg(const me_tile_cfg &c);
 uint64_t cfg_key(const me_tile_cfg &c);
 

@@ -84,7 +84,7 @@ void write_cache(const char *path, const std::string &key, const me_tile_cfg &c)
 }
 
 int run_once(int kind, const me_desc *s, int n, cudaStream_t st) {
-    if (kind == ME_KIND_BATCH) return me_edges_batch(s, n, (me_stream_t)st);
+    if (kind != ME_KIND_SINGLE) return me_edges_batch(s, n, (me_stream_t)st);
     for (int i = 0; i < n; ++i) {
         int rc = me_edges(s[i].img, s[i].w, s[i].h, s[i].stride_words, s[i].edge,
                           s[i].boundary, (me_stream_t)st);
@@ -98,8 +98,8 @@ int run_once(int kind, const me_desc *s, int n, cudaStream_t st) {
 // Apply a cached choice for this device once per process and kind.
 void apply_tune_cache(int kind) {
     static std::mutex mu;
-    static std::atomic<bool> done[2] = {false, false};
-    const int k = kind == ME_KIND_BATCH ? 1 : 0;
+    static std::atomic<bool> done[3] = {false, false, false};
+    const int k = kind == ME_KIND_BATCH || kind == ME_KIND_BATCH_ANY ? kind : ME_KIND_SINGLE;
     if (done[k].load(std::memory_order_acquire)) return;
     std::lock_guard<std::mutex> lk(mu);
     if (done[k].load(std::memory_order_relaxed)) return;
@@ -118,8 +118,11 @@ using namespace me;
 
 extern "C" int me_autotune(int32_t kind, const me_desc *sample, int32_t n, int32_t reps,
                            me_stream_t stream, me_tile_cfg *best) {
-    if ((kind != ME_KIND_SINGLE && kind != ME_KIND_BATCH) || sample == nullptr || n <= 0 ||
-        reps <= 0 || best == nullptr)
+    if ((kind != ME_KIND_SINGLE && kind != ME_KIND_BATCH && kind != ME_KIND_BATCH_ANY) ||
+        sample == nullptr || n <= 0 || reps <= 0 || best == nullptr)
+        return ME_ERR_ARG;
+    // the sample's launches take the configuration of its own batch kind
+    if (kind != ME_KIND_SINGLE && batch_any(sample, n) != (kind == ME_KIND_BATCH_ANY))
         return ME_ERR_ARG;
     DevInfo di;
     int rc = device_info(&di);

@@ -140,3 +140,12 @@ def test_tile_cfg_roundtrip(lib):
     assert L.me_set_tile_cfg(1, ctypes.byref(new)) == 0
     assert lib.me_get_tile_cfg(1).as_dict() == new.as_dict()
     assert L.me_set_tile_cfg(1, ctypes.byref(old)) == 0
+    # the batch kind with narrower accesses keeps a configuration of its own
+    old_any = lib.me_get_tile_cfg(lib.ME_KIND_BATCH_ANY)
+    other = lib.me_tile_cfg(0, 8, 4, 256, 0, 32, 4, 3)
+    assert L.me_set_tile_cfg(lib.ME_KIND_BATCH_ANY, ctypes.byref(other)) == 0
+    assert lib.me_get_tile_cfg(lib.ME_KIND_BATCH_ANY).as_dict() == other.as_dict()
+    assert lib.me_get_tile_cfg(1).as_dict() == old.as_dict()
+    assert L.me_set_tile_cfg(lib.ME_KIND_BATCH_ANY, ctypes.byref(old_any)) == 0
+    assert L.me_set_tile_cfg(3, ctypes.byref(old)) == lib.C["ME_ERR_ARG"]
+    assert L.me_get_tile_cfg(3, ctypes.byref(old)) == lib.C["ME_ERR_ARG"]

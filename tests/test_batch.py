@@ -64,12 +64,27 @@ def image_item(img, b, seed, pad16=True):
     return (img, b), src, dst, (src.ptr(), dst.ptr(), w, h, stride, b)
 
 
+def set_batch_cfg(c):
+    """Give both batch kinds (every image on 128-bit accesses, and some image
+    on narrower ones) the configuration c; return the previous pair."""
+    saved = (_lib.me_get_tile_cfg(_lib.ME_KIND_BATCH), _lib.me_get_tile_cfg(_lib.ME_KIND_BATCH_ANY))
+    for kind in (_lib.ME_KIND_BATCH, _lib.ME_KIND_BATCH_ANY):
+        assert _lib.me_set_tile_cfg(kind, c) == 0, (kind, c.as_dict())
+    return saved
+
+
+def restore_batch_cfg(saved):
+    L = _lib.load()
+    L.me_set_tile_cfg(_lib.ME_KIND_BATCH, saved[0])
+    L.me_set_tile_cfg(_lib.ME_KIND_BATCH_ANY, saved[1])
+
+
 @pytest.mark.parametrize("chunk", [1, 4, 64])
 def test_many_small_images_before_a_tall_one(chunk):
     """40 one-tile images ahead of a 4000 x 40000 image (10000 tiles): the
     tile table then holds one entry per 64 tiles and its first entry
     brackets all 40 small images, which the kernel bisects."""
-    saved = _lib.me_get_tile_cfg(1)
+    saved = None
     parts = []
     rng = np.random.default_rng(5)
     for i in range(40):
@@ -79,12 +94,13 @@ def test_many_small_images_before_a_tall_one(chunk):
     parts.append(image_item(tall, 0, 99))
     imgs, srcs, dsts, items = (list(x) for x in zip(*parts))
     try:
-        assert _lib.me_set_tile_cfg(1, _lib.me_tile_cfg(0, 4, 4, 512, 8, 32, 4, chunk)) == 0
+        saved = set_batch_cfg(_lib.me_tile_cfg(0, 4, 4, 512, 8, 32, 4, chunk))
         assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
         sync()
         check_batch(imgs, srcs, dsts)
     finally:
-        _lib.load().me_set_tile_cfg(1, saved)
+        if saved:
+            restore_batch_cfg(saved)
 
 
 @pytest.mark.parametrize("pad16", [True, False])
@@ -151,8 +167,9 @@ def batch_cfgs():
 
 
 def test_every_batch_configuration():
-    L = _lib.load()
-    saved = _lib.me_get_tile_cfg(1)
+    """Every configuration on a batch of both kinds' images (buffers on and
+    off the 16-byte grid), set for both batch kinds."""
+    saved = set_batch_cfg(_lib.me_get_tile_cfg(_lib.ME_KIND_BATCH))
     imgs, srcs, dsts, items = make_batch(3, 50, 1, 1200, offs=[0, 0, 2, 1])
     # one very wide image forces column strips in the bulk engine
     wide = (np.random.default_rng(9).random((21, 30000)) < 0.5).astype(np.uint8)
@@ -163,7 +180,7 @@ def test_every_batch_configuration():
     descs = _lib.make_descs(items)
     try:
         for c in batch_cfgs():
-            assert _lib.me_set_tile_cfg(1, _lib.me_tile_cfg(*c)) == 0, c
+            set_batch_cfg(_lib.me_tile_cfg(*c))
             for d in dsts:
                 d.t.fill_(int(np.uint32(SENTINEL).view(np.int32)))
             assert _lib.me_edges_batch(descs, len(items)) == 0
@@ -171,7 +188,7 @@ def test_every_batch_configuration():
             check_batch(imgs, srcs, dsts)
         assert _lib.me_device_faults(clear=True) == 0
     finally:
-        L.me_set_tile_cfg(1, saved)
+        restore_batch_cfg(saved)
 
 
 def test_plan_replays():

@@ -69,3 +69,60 @@ def test_autotune_rejects_bad_arguments():
     import ctypes
     assert L.me_autotune(5, None, 0, 1, None, ctypes.byref(best)) == _lib.C["ME_ERR_ARG"]
     assert L.me_autotune(0, None, 1, 1, None, ctypes.byref(best)) == _lib.C["ME_ERR_ARG"]
+
+
+def narrow_sample(seed, n=40):
+    """Images with stride = ceil(w / 32), unpadded: some strides are not whole
+    16-byte groups, so the batch is of the kind ME_KIND_BATCH_ANY."""
+    items, keep = [], []
+    for i, (w, h) in enumerate(S.batch_shapes(seed, n, 16, 600)):
+        img = S.strokes(w, h, 5, i)
+        words = S.pack(img, S.batch_stride(w, False), pad="random", seed=i)
+        src, dst = DevBuf(words), DevBuf(np.zeros_like(words), fill=SENTINEL)
+        keep.append((img, src, dst))
+        items.append((src.ptr(), dst.ptr(), w, h, words.shape[1], 0))
+    assert any(it[4] % 4 for it in items)
+    return items, keep
+
+
+def test_autotune_of_the_narrow_batch_kind():
+    """Tuning ME_KIND_BATCH_ANY on a batch with narrower accesses sets that
+    kind's configuration only, and the batch's edge maps stay exact."""
+    import torch
+    saved = (_lib.me_get_tile_cfg(_lib.ME_KIND_BATCH), _lib.me_get_tile_cfg(_lib.ME_KIND_BATCH_ANY))
+    items, keep = narrow_sample(6)
+    try:
+        best = _lib.me_autotune(_lib.ME_KIND_BATCH_ANY, _lib.make_descs(items), len(items), reps=2)
+        assert best.as_dict() == _lib.me_get_tile_cfg(_lib.ME_KIND_BATCH_ANY).as_dict()
+        assert _lib.me_get_tile_cfg(_lib.ME_KIND_BATCH).as_dict() == saved[0].as_dict()
+        for img, src, dst in keep:
+            dst.t.fill_(int(np.uint32(SENTINEL).view(np.int32)))
+        assert _lib.me_edges_batch(_lib.make_descs(items), len(items)) == 0
+        torch.cuda.synchronize()
+        for img, src, dst in keep:
+            ow = dst.words()
+            check_output_layout(ow, img.shape[1])
+            assert np.array_equal(S.unpack(ow, img.shape[1]), O.edges(img, 0))
+    finally:
+        L = _lib.load()
+        L.me_set_tile_cfg(_lib.ME_KIND_BATCH, saved[0])
+        L.me_set_tile_cfg(_lib.ME_KIND_BATCH_ANY, saved[1])
+
+
+def test_autotune_refuses_a_sample_of_the_other_batch_kind():
+    """A sample's launches use its own kind's configuration, so tuning the
+    other kind on it would time identical launches: refused."""
+    import ctypes
+    L = _lib.load()
+    best = _lib.me_tile_cfg()
+    narrow, keep = narrow_sample(7, 8)
+    wide = []
+    for i, (w, h) in enumerate(S.batch_shapes(8, 8, 16, 300)):
+        words = S.pack(S.strokes(w, h, 3, i), S.batch_stride(w), pad="random", seed=i)
+        src, dst = DevBuf(words), DevBuf(np.zeros_like(words))
+        keep.append((None, src, dst))
+        wide.append((src.ptr(), dst.ptr(), w, h, words.shape[1], 0))
+    assert L.me_autotune(_lib.ME_KIND_BATCH, _lib.make_descs(narrow), len(narrow), 1, None,
+                         ctypes.byref(best)) == _lib.C["ME_ERR_ARG"]
+    assert L.me_autotune(_lib.ME_KIND_BATCH_ANY, _lib.make_descs(wide), len(wide), 1, None,
+                         ctypes.byref(best)) == _lib.C["ME_ERR_ARG"]
