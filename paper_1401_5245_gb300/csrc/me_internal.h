@@ -302,6 +302,24 @@ int batch_grid(const me_tile_cfg &cfg, const DevInfo &di, int64_t total_tasks, b
 int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_arena,
                int64_t *total_tasks, bool *any, int *bad);
 
+// By-value arguments of the register-window batch kernel, which reads them
+// from the constant bank (no registers held).  Warp w takes work items w,
+// w + W, w + 2W, ... of the grid's W warps: items below nchunks are chunks
+// of `chunk` tiles (item k: tiles k * chunk ..), the rest single tiles
+// (item k: tile k + chunked - nchunks), up to `total` tiles.
+struct BatchArgs {
+    int32_t total;        // tiles of the batch
+    int32_t chunk;        // tiles per chunk
+    int32_t shift;        // tiles per image-table entry, log2
+    int32_t nchunks;      // chunk items
+    int32_t chunked;      // nchunks * chunk: tiles covered by chunks
+};
+// The split for a grid: whole rounds of chunks (one per warp each) when
+// the batch has at least one, else the whole chunks its tiles make; the
+// tiles left over go one at a time, so that the warps' last pieces of work
+// differ by one tile rather than a chunk.
+BatchArgs batch_args(const void *host_arena, int grid, int threads);
+
 // How one batch launches under a tile configuration: grid, threads,
 // dynamic shared memory, arena size and kernel.
 struct BatchSetup {
@@ -311,6 +329,7 @@ struct BatchSetup {
     const void *fn = nullptr;
     int stage_words = 0;
     bool any = false;           // register window: the kernel with 32-bit tiles
+    BatchArgs args = {};        // register window: set by fill_arena
 };
 // Neither reads the images' geometry beyond n: descriptors are checked by
 // fill_arena, which also fixes the grid of a one-chunk-per-warp launch.

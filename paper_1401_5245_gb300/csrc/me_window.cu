@@ -105,73 +105,86 @@ cudaError_t launch_window(int mode, const Geo &g, const Outs &o,
 __device__ unsigned int g_me_window_faults = 0;
 constexpr unsigned int kFaultUnalignedTile = 2u;
 
+// Tiles c0 .. t1 - 1 of the batch, which are consecutive.
+template <int RPT, bool ANY>
+__device__ __forceinline__ void batch_tiles(const BDesc *__restrict__ descs,
+                                            const int32_t *__restrict__ block_image, int shift,
+                                            int c0, int t1, int lane) {
+    // the image of tile c0: bisect the images the table brackets it with
+    int i = block_image[c0 >> shift];
+    int hi = block_image[(c0 >> shift) + 1];
+    while (i < hi) {
+        const int mid = (i + hi + 1) >> 1;
+        if (descs[mid].task_base <= c0) i = mid; else hi = mid - 1;
+    }
+    for (int t = c0; t < t1; ++t) {
+        while (t >= descs[i].task_base + descs[i].ntasks) ++i;
+        // the 64-byte descriptor as four 128-bit loads
+        const uint4 *dv = reinterpret_cast<const uint4 *>(descs + i);
+        const uint4 d0 = dv[0], d1 = dv[1], d2 = dv[2], d3 = dv[3];
+        Geo g;
+        g.img = reinterpret_cast<const uint32_t *>(((uint64_t)d0.y << 32) | d0.x);
+        g.w = 0;
+        g.segs = (int)d1.x;
+        g.h = (int)d1.y;
+        g.stride = (int)d1.z;
+        g.nw = (int)d1.w;
+        g.lastmask = d2.x;
+        g.fill = d2.y;
+        g.vw = (int)(d2.z & 0xff);
+        g.vec16 = (int)((d2.z >> 8) & 1);
+        g.vec8 = (int)((d2.z >> 9) & 1);
+        g.seg_w = (int)d2.w;
+        g.ncb = (int)d3.x;
+        g.nv = (int)d3.y;
+        Outs o;
+        o.p[0] = reinterpret_cast<uint32_t *>(((uint64_t)d0.w << 32) | d0.z);
+        o.p[1] = o.p[2] = o.p[3] = nullptr;
+        const int local = t - (int)d3.z;             // task_base
+        // rows of at most 32 vector columns have one column block: no
+        // division
+        const int cb = g.ncb == 1 ? 0 : local % g.ncb;
+        const int rb = g.ncb == 1 ? local : local / g.ncb;
+        if (g.vec16) {
+            window_tile<4, RPT, MODE_EDGE, 16>(g, o, cb, rb, lane);
+        } else if constexpr (ANY) {
+            if (g.vec8)
+                window_tile<4, RPT, MODE_EDGE, 8>(g, o, cb, rb, lane);
+            else
+                window_tile<4, RPT, MODE_EDGE, 4>(g, o, cb, rb, lane);
+        } else if (lane == 0)
+            atomicOr(&g_me_window_faults, kFaultUnalignedTile);
+    }
+}
+
 // Two 512-thread CTAs per SM for 4 rows per lane (64 registers).  ANY:
 // images whose rows are not whole 16-byte groups (or whose buffers are not
 // 16-byte aligned) may occur, so the kernel also carries the tile that
 // moves four words per lane as 32-bit accesses; batches without such images
 // take the kernel without it, whose registers it would otherwise raise.
+// The loop's constants come by value (BatchArgs), from the constant bank:
+// loaded from the arena they would hold registers the tile needs.
 template <int RPT, bool ANY>
 __global__ void __launch_bounds__(512, RPT == 4 ? 2 : 1)
-k_batch(const BatchHeader *__restrict__ hdr) {
+k_batch(const BatchHeader *__restrict__ hdr, const BatchArgs a) {
     const BDesc *descs = reinterpret_cast<const BDesc *>(hdr + 1);
     const int32_t *block_image = reinterpret_cast<const int32_t *>(descs + hdr->n);
-    const int T = hdr->total_tasks;
-    const int C = hdr->chunk_tiles;
-    const int shift = hdr->block_shift;
     const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int64_t step = (int64_t)((gridDim.x * (unsigned)blockDim.x) >> 5) * C;
-    for (int64_t c0 = (int64_t)warp * C; c0 < T; c0 += step) {
-        const int t1 = (int)min(c0 + C, (int64_t)T);
-        // the image of tile c0: bisect the images the table brackets it with
-        int i = block_image[c0 >> shift];
-        int hi = block_image[(c0 >> shift) + 1];
-        while (i < hi) {
-            const int mid = (i + hi + 1) >> 1;
-            if (descs[mid].task_base <= c0) i = mid; else hi = mid - 1;
-        }
-        for (int t = (int)c0; t < t1; ++t) {
-            while (t >= descs[i].task_base + descs[i].ntasks) ++i;
-            // the 64-byte descriptor as four 128-bit loads
-            const uint4 *dv = reinterpret_cast<const uint4 *>(descs + i);
-            const uint4 d0 = dv[0], d1 = dv[1], d2 = dv[2], d3 = dv[3];
-            Geo g;
-            g.img = reinterpret_cast<const uint32_t *>(((uint64_t)d0.y << 32) | d0.x);
-            g.w = 0;
-            g.segs = (int)d1.x;
-            g.h = (int)d1.y;
-            g.stride = (int)d1.z;
-            g.nw = (int)d1.w;
-            g.lastmask = d2.x;
-            g.fill = d2.y;
-            g.vw = (int)(d2.z & 0xff);
-            g.vec16 = (int)((d2.z >> 8) & 1);
-            g.vec8 = (int)((d2.z >> 9) & 1);
-            g.seg_w = (int)d2.w;
-            g.ncb = (int)d3.x;
-            g.nv = (int)d3.y;
-            Outs o;
-            o.p[0] = reinterpret_cast<uint32_t *>(((uint64_t)d0.w << 32) | d0.z);
-            o.p[1] = o.p[2] = o.p[3] = nullptr;
-            const int local = t - (int)d3.z;             // task_base
-            // rows of at most 32 vector columns have one column block: no
-            // division
-            const int cb = g.ncb == 1 ? 0 : local % g.ncb;
-            const int rb = g.ncb == 1 ? local : local / g.ncb;
-            if (g.vec16) {
-                window_tile<4, RPT, MODE_EDGE, 16>(g, o, cb, rb, lane);
-            } else if constexpr (ANY) {
-                if (g.vec8)
-                    window_tile<4, RPT, MODE_EDGE, 8>(g, o, cb, rb, lane);
-                else
-                    window_tile<4, RPT, MODE_EDGE, 4>(g, o, cb, rb, lane);
-            } else if (lane == 0)
-                atomicOr(&g_me_window_faults, kFaultUnalignedTile);
-        }
+    const unsigned warp = (blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5;
+    const unsigned W = (gridDim.x * (unsigned)blockDim.x) >> 5;
+    // Tile indices are below 2^31 and item indices below the tiles plus a
+    // grid's warps, so no unsigned sum below wraps.
+    for (unsigned k = warp;; k += W) {
+        const bool chunk = k < (unsigned)a.nchunks;
+        const unsigned c0 = chunk ? k * (unsigned)a.chunk
+                                  : k + (unsigned)(a.chunked - a.nchunks);
+        if (c0 >= (unsigned)a.total) break;
+        batch_tiles<RPT, ANY>(descs, block_image, a.shift, (int)c0,
+                              (int)(c0 + (chunk ? (unsigned)a.chunk : 1u)), lane);
     }
 }
 
-using BatchFn = void (*)(const BatchHeader *);
+using BatchFn = void (*)(const BatchHeader *, BatchArgs);
 
 static BatchFn pick_batch(int rpt, bool any) {
     switch (rpt) {
@@ -312,6 +325,20 @@ int plan_batch(const me_desc *descs, int n, const me_tile_cfg &cfg, void *host_a
     if (total_tasks) *total_tasks = total;
     if (any) *any = narrow;
     return ME_OK;
+}
+
+BatchArgs batch_args(const void *host_arena, int grid, int threads) {
+    const BatchHeader *hdr = static_cast<const BatchHeader *>(host_arena);
+    BatchArgs a;
+    a.total = hdr->total_tasks;
+    a.chunk = hdr->chunk_tiles;
+    a.shift = hdr->block_shift;
+    const int64_t step = (int64_t)grid * (threads / 32) * a.chunk;
+    int64_t chunked = step > 0 ? (int64_t)a.total / step * step : 0;
+    if (chunked == 0) chunked = (int64_t)a.total / a.chunk * a.chunk;
+    a.chunked = (int32_t)chunked;
+    a.nchunks = (int32_t)(chunked / a.chunk);
+    return a;
 }
 
 unsigned int window_fault_flags(bool clear) {
