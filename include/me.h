@@ -269,8 +269,8 @@ typedef struct me_desc {
 } me_desc;
 
 /*
- * me_edges on n images of any sizes in ONE persistent kernel launch,
- * replayed from a CUDA graph.  descs is a HOST array, copied
+ * me_edges on n images of any sizes in ONE persistent kernel launch.
+ * descs is a HOST array, copied
  * before the call returns (the caller may reuse it at once).  Image and
  * edge buffers are caller-owned device memory, checked for NULL, size and
  * overlap within each descriptor but not against one another: two
@@ -279,9 +279,12 @@ typedef struct me_desc {
  * 128-bit (else 64-bit) accesses are used per image where its buffers
  * allow them, as for me_edges.
  *
- * The library owns a pinned staging ring, a device descriptor arena and a
- * graph cache keyed by (capacity bucket, tile configuration); all of them
- * live until me_shutdown().  n == 0 returns ME_OK with nothing enqueued.
+ * The tile configuration is that of the batch's kind: ME_KIND_BATCH if
+ * every image allows 128-bit accesses, else ME_KIND_BATCH_ANY.  The
+ * library owns a pinned staging ring, a device descriptor arena and (for
+ * the bulk-copy engine) a graph cache keyed by tile configuration; all of
+ * them live until me_shutdown().  n == 0 returns ME_OK with nothing
+ * enqueued.
  */
 int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream);
 
@@ -289,7 +292,7 @@ int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream);
  * A batch planned once and replayed many times: the descriptors are
  * uploaded to a device arena owned by the plan, and every me_batch_run is
  * one graph launch of the kernel alone.  The plan keeps the tile
- * configuration current at creation.  Runs of one plan on different
+ * configuration of its batch kind current at creation.  Runs of one plan on different
  * streams must be ordered by the caller.
  */
 typedef struct me_batch_plan me_batch_plan;
