@@ -4,7 +4,7 @@
 One step = one me_edges_batch call over a batch of 4096 uneven 1-bit images
 (w, h log-uniform on [16, 4096], glyph strokes, rows padded to 16 bytes):
 the whole fused path (mask, four fundamental edges, OR) in one persistent
-kernel launched from a CUDA graph, inputs resident in HBM.  Prints one
+kernel launch, inputs resident in HBM.  Prints one
 JSON line (rank 0).  Extra legs, timed after the main region: the staged
 five-pass form on the same batch, the fused kernel on one 32768x32768
 image, the batch kernel alone (roofline), host-buffer end-to-end, clocks,
@@ -38,8 +38,7 @@ METRIC = ("Gpixel/s (bit-exact), fused+batched vs staged BitBlt; "
 UNIT = "Gpixel/s"
 N_IMAGES = 4096
 WORKLOAD = ("batch of 4096 uneven 1bpp images, w and h log-uniform on [16, 4096], "
-            "glyph-stroke content, rows padded to 16 bytes, one persistent launch "
-            "under a CUDA graph")
+            "glyph-stroke content, rows padded to 16 bytes, one persistent launch")
 
 
 # ---------------------------------------------------------------- ranks
