@@ -318,7 +318,7 @@ int me_batch_plan_destroy(me_batch_plan *plan);
  *                    byte aligned offsets keep the 128-bit path); the image
  *                    takes h * stride_words words from there; w, h,
  *                    stride_words, boundary as me_desc.
- * chunk_bytes        input bytes per pipeline chunk (0: 32 MiB); images are
+ * chunk_bytes        input bytes per pipeline chunk (0: 16 MiB); images are
  *                    grouped into chunks in order, at least one per chunk.
  * stream             the work starts after what `stream` already holds.
  *
