@@ -66,7 +66,10 @@ constexpr size_t kAlign = 256;
 constexpr int kShards = 16;
 // A poller watches its request this long before it sleeps: most requests
 // finish meanwhile, and the completion thread then makes no wake-up call.
-constexpr int kSpinUs = 30;
+// At saturation a request takes about 110-150 us in the server; 100 us
+// measured 4-6% more requests per second than 30 us, and 300 or 1000 us no
+// more than 100.
+constexpr int kSpinUs = 100;
 
 enum State { QUEUED, ADMITTED, DONE, FAILED };
 
