@@ -4,6 +4,8 @@
 // the persistent kernel searches.  Addresses are made up (never
 // dereferenced): images 16 MiB apart, offset from the 16-byte grid as each
 // case needs.
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <random>
 #include <vector>
@@ -163,6 +165,64 @@ int main() {
         }
         if (fails) break;
     }
+
+    // 3. the work items of a launch (me::batch_args for its grid, walked
+    // with the persistent kernel's own arithmetic for every warp): every
+    // tile taken exactly once, chunks only below `chunked`, and the warps'
+    // tile counts at most one chunk apart
+    for (int round = 0; round < 200 && fails == 0; ++round) {
+        const int n = 1 + (int)(rng() % 400);
+        std::vector<Img> imgs;
+        for (int k = 0; k < n; ++k) {
+            const int w = 1 + (int)(rng() % 3000);
+            const int h = 1 + (int)(rng() % (rng() % 8 == 0 ? 5000 : 200));
+            imgs.push_back({0, ((w + 31) / 32 + 3) / 4 * 4, w, h});
+        }
+        const int chunks[] = {1, 2, 3, 4, 8};
+        Plan p;
+        if (!plan(make(imgs), batch_cfg(4, 4, chunks[rng() % 5]), &p)) {
+            expect(false, "random batch planned");
+            break;
+        }
+        const int grids[] = {1, 7, 152, 304, 1216};
+        const int threads[] = {128, 256, 512};
+        const int grid = grids[rng() % 5], thr = threads[rng() % 3];
+        const me::BatchArgs a = me::batch_args(p.arena.data(), grid, thr);
+        const unsigned W = (unsigned)grid * (unsigned)thr / 32;
+        const int64_t T = p.total;
+        expect(a.total == T && a.chunk == p.hdr()->chunk_tiles, "arguments from the header");
+        expect(a.chunked % a.chunk == 0 && a.nchunks * a.chunk == a.chunked && a.chunked <= T,
+               "chunks cover a prefix");
+        std::vector<int> seen((size_t)T, 0);
+        int64_t lo = INT64_MAX, hi = 0;
+        for (unsigned warp = 0; warp < W; ++warp) {
+            int64_t mine = 0;
+            for (unsigned k = warp;; k += W) {
+                const bool chunk = k < (unsigned)a.nchunks;
+                const unsigned c0 = chunk ? k * (unsigned)a.chunk
+                                          : k + (unsigned)(a.chunked - a.nchunks);
+                if (c0 >= (unsigned)a.total) break;
+                const unsigned t1 = c0 + (chunk ? (unsigned)a.chunk : 1u);
+                if (chunk && t1 > (unsigned)a.chunked) expect(false, "chunk inside the prefix");
+                for (unsigned t = c0; t < t1 && t < (unsigned)T; ++t) ++seen[t];
+                mine += t1 - c0;
+            }
+            lo = std::min(lo, mine);
+            hi = std::max(hi, mine);
+        }
+        for (int64_t t = 0; t < T; ++t)
+            if (seen[(size_t)t] != 1) {
+                std::printf("round %d: tile %lld taken %d times (T %lld, W %u, C %d)\n", round,
+                            (long long)t, seen[(size_t)t], (long long)T, W, a.chunk);
+                expect(false, "every tile once");
+                break;
+            }
+        if (hi - lo > a.chunk)
+            std::printf("round %d: warps take %lld to %lld tiles (C %d)\n", round, (long long)lo,
+                        (long long)hi, a.chunk);
+        expect(hi - lo <= a.chunk, "warps' work at most one chunk apart");
+    }
+
     if (fails == 0) std::printf("ok\n");
     return fails == 0 ? 0 : 1;
 }
