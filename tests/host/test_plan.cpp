@@ -113,6 +113,12 @@ int main() {
         }
         if (p.any != c.want_any) std::printf("case '%s': any = %d\n", c.name, (int)p.any);
         expect(p.any == c.want_any, c.name);
+        // the batch kind, which picks the tile configuration, agrees with
+        // the plan's choice of kernel form wherever the access width is free
+        if (c.vec_words == 4) {
+            const std::vector<me_desc> d = make(c.imgs);
+            expect(me::batch_any(d.data(), (int)d.size()) == c.want_any, "batch kind");
+        }
         for (size_t k = 0; k < c.imgs.size(); ++k) {
             const int bits = (p.bd()[k].vw >> 8) & 3;
             expect((p.bd()[k].vw & 0xff) == 4, "4 words per lane");
