@@ -328,13 +328,18 @@ def test_load_generator_zero_copy_every_result_is_the_oracles(pool):
 
 
 def test_random_interleaving_of_every_call(pool):
-    """Six threads each run a random mix of copying and zero-copy submits,
-    polls with random timeouts (0, short, unlimited), views and releases,
-    and cancels of their own requests, against a budget and a staging pool
-    small enough that requests queue for memory and spill into heap
-    memory.  Every result collected equals the oracle's; the server's
-    counters add up; close drains what is left."""
+    """Six threads each run a random mix of copying, zero-copy and direct
+    submits, polls with random timeouts (0, short, unlimited), views and
+    releases, and cancels of their own requests, against a budget and a
+    staging pool small enough that requests queue for memory and spill into
+    heap memory.  Every result collected equals the oracle's; the server's
+    counters add up; close drains what is left.  Direct requests' pinned
+    buffers stay alive until close (a cancelled one may still be written)."""
+    import torch
     want = {id(im): oracle_words(im) for im in pool}
+    small = [im for im in pool if im.packed_bytes <= 200_000]
+    pinned_in = {id(im): pinned_copy(im.words) for im in small}
+    outs = []              # every direct output buffer, kept until close
     page = max(pool, key=lambda im: im.packed_bytes)
     span = (page.packed_bytes + 255) // 256 * 256
     srv = _lib.Server(hbm_budget_bytes=6 * span, staging_bytes=8 * span, max_inflight=2,
@@ -343,17 +348,25 @@ def test_random_interleaving_of_every_call(pool):
 
     def worker(seed):
         g = np.random.default_rng(seed)
-        live = []          # (ticket, image, zero_copy)
+        live = []          # (ticket, image, zero_copy, direct output or None)
         done = cancelled = 0
         try:
             for _ in range(150):
                 op = g.random()
                 if op < 0.45 or not live:
                     im = pool[int(g.integers(0, len(pool)))]
-                    if g.random() < 0.5:
+                    if id(im) in pinned_in and g.random() < 0.35:
+                        t_out = torch.empty(im.words.size, dtype=torch.int32).pin_memory()
+                        outs.append(t_out)
+                        out = t_out.numpy().view(np.uint32).reshape(im.words.shape)
+                        rc, t = srv.submit_direct(pinned_in[id(im)][1], out, im.w, im.h,
+                                                  im.stride_words, im.boundary)
+                        assert rc == 0, _lib.status_string(rc)
+                        live.append((t, im, False, out))
+                    elif g.random() < 0.5:
                         rc, t = srv.submit(im.words, im.w, im.h, im.stride_words, im.boundary)
                         assert rc == 0, _lib.status_string(rc)
-                        live.append((t, im, False))
+                        live.append((t, im, False, None))
                     else:
                         rc, t, dst = srv.reserve(im.w, im.h, im.stride_words, im.boundary)
                         if rc == _lib.C["ME_PENDING"]:
@@ -361,14 +374,20 @@ def test_random_interleaving_of_every_call(pool):
                         assert rc == 0, _lib.status_string(rc)
                         dst[...] = im.words
                         assert srv.commit(t) == 0
-                        live.append((t, im, True))
+                        live.append((t, im, True, None))
                 elif op < 0.9:
                     k = int(g.integers(0, len(live)))
-                    t, im, zc = live[k]
+                    t, im, zc, out = live[k]
                     # no unlimited wait here: a request in heap memory waits
                     # for staging that other threads' uncollected results hold
                     timeout = int(g.choice([0, 200, 5000]))
-                    if zc or g.random() < 0.3:
+                    if out is not None and g.random() < 0.5:
+                        rc, tm = srv.poll_direct(t, timeout)
+                        if rc in (_lib.C["ME_PENDING"], _lib.C["ME_TIMEOUT"]):
+                            continue
+                        assert rc == 0, _lib.status_string(rc)
+                        assert np.array_equal(out, want[id(im)])
+                    elif zc or g.random() < 0.3:
                         rc, tm, view = srv.poll_view(t, im.h, im.stride_words, timeout)
                         if rc in (_lib.C["ME_PENDING"], _lib.C["ME_TIMEOUT"]):
                             continue
@@ -396,11 +415,11 @@ def test_random_interleaving_of_every_call(pool):
             while live:
                 assert time.monotonic() < deadline, "requests never finished"
                 keep = []
-                for t, im, zc in live:
+                for t, im, zc, out in live:
                     res = np.empty_like(im.words)
                     rc, _ = srv.poll(t, res, 0)
                     if rc == _lib.C["ME_PENDING"]:
-                        keep.append((t, im, zc))
+                        keep.append((t, im, zc, out))
                         continue
                     assert rc == 0, _lib.status_string(rc)
                     assert np.array_equal(res, want[id(im)])
@@ -424,6 +443,7 @@ def test_random_interleaving_of_every_call(pool):
         assert st["peak_bytes"] <= 6 * span
     finally:
         assert srv.close(-1) == 0
+        del outs
 
 
 # ------------------------------------------------------------ direct submit
