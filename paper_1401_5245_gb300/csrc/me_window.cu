@@ -167,6 +167,9 @@ __device__ __forceinline__ void batch_tiles(const BDesc *__restrict__ descs,
 template <int RPT, bool ANY>
 __global__ void __launch_bounds__(512, RPT == 4 ? 2 : 1)
 k_batch(const BatchHeader *__restrict__ hdr, const BatchArgs a) {
+    // launched while the kernel before it on the stream may still run
+    // (programmatic dependent launch): wait for it before any global access
+    pdl_enter();
     const BDesc *descs = reinterpret_cast<const BDesc *>(hdr + 1);
     const int32_t *block_image = reinterpret_cast<const int32_t *>(descs + hdr->n);
     const int lane = threadIdx.x & 31;

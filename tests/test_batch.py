@@ -150,6 +150,49 @@ def test_repeated_calls_reuse_graphs_and_slots():
             check_batch(imgs, srcs, dsts)
 
 
+def test_the_same_batch_again_reads_its_images_anew():
+    """The same descriptors submitted again launch on the plan already on the
+    device: each call's edge maps still come from the images as they are at
+    that call (new content written into the same buffers before every call,
+    outputs reset to a sentinel), with another batch submitted in between
+    and a change of one descriptor (an output moved) planned afresh."""
+    import torch
+    from tests.gpu_util import GUARD
+    imgs, srcs, dsts, items = make_batch(21, 50, 1, 600)
+    other = make_batch(22, 30, 1, 400)
+    descs = _lib.make_descs(items)
+    rng = np.random.default_rng(4)
+    sentinel = int(np.uint32(SENTINEL).view(np.int32))
+    for rep in range(5):
+        fresh = []
+        for (img, b), src, it in zip(imgs, srcs, items):
+            new = (rng.random(img.shape) < 0.3 + 0.1 * rep).astype(np.uint8)
+            words = S.pack(new, it[4], pad="random", seed=rep)
+            src.t[GUARD + src.off:GUARD + src.off + src.n] = \
+                torch.from_numpy(words.view(np.int32).ravel()).to(src.t.device)
+            fresh.append((new, b))
+        for d in dsts:
+            d.t.fill_(sentinel)
+        assert _lib.me_edges_batch(descs, len(items)) == 0
+        if rep % 2 == 1:
+            assert _lib.me_edges_batch(_lib.make_descs(other[3]), len(other[3])) == 0
+        sync()
+        check_batch(fresh, srcs, dsts)
+        if rep % 2 == 1:
+            check_batch(*other[:3])
+    # one output moved: a new plan, the right buffer written
+    moved = DevBuf(np.zeros_like(dsts[0].words()), fill=SENTINEL)
+    items2 = list(items)
+    items2[0] = (items[0][0], moved.ptr()) + tuple(items[0][2:])
+    for d in dsts:
+        d.t.fill_(sentinel)
+    assert _lib.me_edges_batch(_lib.make_descs(items2), len(items2)) == 0
+    sync()
+    check_batch(fresh[:1], srcs[:1], [moved])
+    check_batch(fresh[1:], srcs[1:], dsts[1:])
+    assert (dsts[0].words() == np.uint32(SENTINEL)).all()
+
+
 def batch_cfgs():
     out = []
     chunks = itertools.cycle([1, 3, 4, 64])
