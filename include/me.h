@@ -283,16 +283,22 @@ typedef struct me_desc {
  * every image allows 128-bit accesses, else ME_KIND_BATCH_ANY.  The
  * library owns a pinned staging ring, a device descriptor arena and (for
  * the bulk-copy engine) a graph cache keyed by tile configuration; all of
- * them live until me_shutdown().  n == 0 returns ME_OK with nothing
- * enqueued.
+ * them live until me_shutdown().  A batch submitted again with the same
+ * descriptors (byte for byte) under the same configuration launches on the
+ * plan already on the device, without planning or uploading it; its images
+ * are read and its edge maps written as on any call.  The kernel may be
+ * placed while the kernel before it on the stream finishes (programmatic
+ * dependent launch) and waits for it before touching memory.  n == 0
+ * returns ME_OK with nothing enqueued.
  */
 int me_edges_batch(const me_desc *descs, int32_t n, me_stream_t stream);
 
 /*
  * A batch planned once and replayed many times: the descriptors are
  * uploaded to a device arena owned by the plan, and every me_batch_run is
- * one graph launch of the kernel alone.  The plan keeps the tile
- * configuration of its batch kind current at creation.  Runs of one plan on different
+ * one launch of the kernel alone (by programmatic dependent launch; the
+ * bulk-copy engine's from a graph).  The plan keeps the tile configuration
+ * of its batch kind current at creation.  Runs of one plan on different
  * streams must be ordered by the caller.
  */
 typedef struct me_batch_plan me_batch_plan;
