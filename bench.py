@@ -933,7 +933,10 @@ def run_ours(args, rank, world, local_rank):
         if rc != 0:
             raise _lib.MeError(rc, "me_edges_batch_host")
     e2e_step()
-    e2e_reps = max(3, min(args.steps, 20))
+    # the whole-job mean over 50 steps (about 0.1 s): on some boxes about one
+    # step in a hundred takes several milliseconds on the host side, which a
+    # mean over fewer steps over- or under-represents
+    e2e_reps = 50
     barrier(dist)
     rep_s = []
     t0 = time.perf_counter()

@@ -92,15 +92,17 @@ int fill_arena(const me_desc *descs, int n, Setup &s, void *host) {
     return rc;
 }
 
-cudaError_t launch_planned(const Setup &s, void *arena_dev, cudaStream_t stream) {
+cudaError_t launch_planned(const Setup &s, void *arena_dev, cudaStream_t stream, bool pdl) {
     void *arena = arena_dev;
     KDescB none = {};
     int zero = 0, stage_words = s.stage_words, stages = s.cfg.stages;
     BatchArgs args = s.args;
     void *regs_args[] = {&arena, &args};
     void *bulk_args[] = {&arena, &none, &zero, &stage_words, &stages};
-    if (s.cfg.engine == ME_ENGINE_BULK)
-        return cudaLaunchKernel(s.fn, dim3(s.grid), dim3(s.threads), bulk_args, s.smem, stream);
+    if (s.cfg.engine == ME_ENGINE_BULK || !pdl)
+        return cudaLaunchKernel(s.fn, dim3(s.grid), dim3(s.threads),
+                                s.cfg.engine == ME_ENGINE_BULK ? bulk_args : regs_args, s.smem,
+                                stream);
     // the register-window kernel waits for the kernel before it on the
     // stream before its first global access (griddepcontrol.wait), so it
     // may be launched while that one finishes (programmatic dependent launch)
@@ -254,11 +256,13 @@ int BatchRing::launch(const me_desc *descs, int n, cudaStream_t stream) {
                 continue;
             // the upload is long done unless the batch came back at once
             // from another stream
+            bool wait = false;
             if (cudaEventQuery(s.copied) != cudaSuccess) {
                 cudaGetLastError();
                 if ((e = cudaStreamWaitEvent(stream, s.copied, 0)) != cudaSuccess) return fail(e);
+                wait = true;
             }
-            if ((e = launch_planned(s.su, s.dev, stream)) != cudaSuccess) return fail(e);
+            if ((e = launch_planned(s.su, s.dev, stream, !wait)) != cudaSuccess) return fail(e);
             if ((e = cudaEventRecord(s.done, stream)) != cudaSuccess) return fail(e);
             s.pending = true;
             return ME_OK;
@@ -301,7 +305,8 @@ int BatchRing::launch(const me_desc *descs, int n, cudaStream_t stream) {
         return fail(e);
     if ((e = cudaEventRecord(slot.copied, copy_)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamWaitEvent(stream, slot.copied, 0)) != cudaSuccess) return fail(e);
-    e = graph ? cudaGraphLaunch(graph->exec, stream) : launch_planned(su, slot.dev, stream);
+    e = graph ? cudaGraphLaunch(graph->exec, stream)
+              : launch_planned(su, slot.dev, stream, false);    // after the event wait
     if (e != cudaSuccess) return fail(e);
     if ((e = cudaEventRecord(slot.done, stream)) != cudaSuccess) return fail(e);
     slot.pending = true;

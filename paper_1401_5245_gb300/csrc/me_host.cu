@@ -304,7 +304,9 @@ extern "C" int me_edges_batch_host(const uint32_t *host_in, uint32_t *host_out,
         char *dout = p->slot[s] + p->cap;
         if (k > 0 && (e = upload(k)) != cudaSuccess) return fail_drain(p, fail(e));
         if ((e = cudaStreamWaitEvent(p->comp, p->up_done[s], 0)) != cudaSuccess) return fail_drain(p, fail(e));
-        if ((e = launch_planned(setups[k], p->plan_dev + arena_at[k], p->comp)) != cudaSuccess)
+        // a plain launch: an event wait stands before every chunk's kernel
+        if ((e = launch_planned(setups[k], p->plan_dev + arena_at[k], p->comp, false)) !=
+            cudaSuccess)
             return fail_drain(p, fail(e));
         if ((e = cudaEventRecord(p->comp_done[s], p->comp)) != cudaSuccess) return fail_drain(p, fail(e));
         if ((e = cudaStreamWaitEvent(p->down, p->comp_done[s], 0)) != cudaSuccess) return fail_drain(p, fail(e));

@@ -337,7 +337,11 @@ int setup_batch(const me_desc *descs, int n, me_tile_cfg cfg, BatchSetup *s);
 // Write the arena of a batch (s.arena bytes) into host memory.
 int fill_arena(const me_desc *descs, int n, BatchSetup &s, void *host);
 // Launch the batch kernel over an arena already in device memory.
-cudaError_t launch_planned(const BatchSetup &s, void *arena_dev, cudaStream_t stream);
+// pdl: the register-window kernel may be placed while the kernel before it
+// on the stream finishes (it waits for it on entry); worth it only where
+// no other operation stands between the two.
+cudaError_t launch_planned(const BatchSetup &s, void *arena_dev, cudaStream_t stream,
+                           bool pdl = true);
 
 // A ring of batch launch slots (pinned staging, device arena, cached
 // graphs).  launch() is thread-safe; a slot is reused only after its last
