@@ -298,16 +298,33 @@ def batch_sample(batch, dev_out, offs, every=16):
     return res
 
 
+class no_gc:
+    """Python's garbage collector off while a region is timed (as timeit
+    does): a full collection in this process, which holds the batch's
+    thousands of images, stalls the host for milliseconds."""
+
+    def __enter__(self):
+        import gc
+        self.was = gc.isenabled()
+        gc.disable()
+
+    def __exit__(self, *exc):
+        import gc
+        if self.was:
+            gc.enable()
+
+
 def time_events(fn, reps, stream):
     import torch
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    a.record(stream)
-    for _ in range(reps):
-        fn()
-    b.record(stream)
-    b.synchronize()
+    with no_gc():
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
     return a.elapsed_time(b) / 1e3 / reps
 
 
@@ -871,11 +888,12 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    with no_gc():
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
     barrier(dist)
     t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
     t_step_max = reduce_max(dist, t_step, device)
@@ -939,12 +957,13 @@ def run_ours(args, rank, world, local_rank):
     e2e_reps = 50
     barrier(dist)
     rep_s = []
-    t0 = time.perf_counter()
-    for _ in range(e2e_reps):
-        t1 = time.perf_counter()
-        e2e_step()
-        rep_s.append(time.perf_counter() - t1)
-    t_e2e = (time.perf_counter() - t0) / e2e_reps
+    with no_gc():
+        t0 = time.perf_counter()
+        for _ in range(e2e_reps):
+            t1 = time.perf_counter()
+            e2e_step()
+            rep_s.append(time.perf_counter() - t1)
+        t_e2e = (time.perf_counter() - t0) / e2e_reps
     e2e_exact = bool(np.array_equal(host_out.numpy(), dev_out.cpu().numpy()))
     # the host link itself on this machine: plain pinned copies of the same bytes
     # (the end-to-end number cannot beat these; the link differs by box)
