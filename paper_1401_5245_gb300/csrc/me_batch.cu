@@ -287,12 +287,12 @@ int BatchRing::launch(const me_desc *descs, int n, cudaStream_t stream) {
     // launched directly (measured as fast as a graph launch).
     GraphEntry *graph = nullptr;
     if (su.cfg.engine == ME_ENGINE_BULK) {
-        const uint64_t key = (cfg_key(su.cfg) * 31 + (uint64_t)su.grid) * 2 + (su.any ? 1 : 0);
-        auto it = slot.graphs.find(key);
+        const uint64_t gkey = (key * 31 + (uint64_t)su.grid) * 2 + (su.any ? 1 : 0);
+        auto it = slot.graphs.find(gkey);
         if (it == slot.graphs.end()) {
             GraphEntry ge;
             if ((e = build_graph(slot.dev, su, &ge)) != cudaSuccess) return fail(e);
-            it = slot.graphs.emplace(key, ge).first;
+            it = slot.graphs.emplace(gkey, ge).first;
         }
         graph = &it->second;
     }
